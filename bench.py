@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the OSCAR hot path on GB300.
+
+One step = one OSCAR global time step: a viscous-drag step followed by the
+capillary-relaxation loop (up to N sub-steps, early exit on E_k < 1e-4), on
+the 3D constricted square channel (256x64x64 cells over 1600x100x100 um,
+sinusoidal constriction to 30 %, CO2 slug, mixed precision). Metric:
+cell-updates/s (fluid cells advanced through one drag step or one relaxation
+sub-step, per second).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl oscar|reference]
+
+N > 1 (under torchrun) runs one independent replica per GPU (the method has
+no exchange step between instances): weak scaling, max-over-ranks time.
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2105_10576_gb300 import inputs  # noqa: E402
+
+METRIC = "cell-updates/s (OSCAR drag step + capillary relaxation)"
+UNIT = "cell-updates/s"
+
+
+def make_workload(name: str):
+    if name == "constriction_3d":
+        c = inputs.constricted_channel_3d()
+        desc = ("3D constricted square channel 256x64x64 over 1600x100x100 um, constriction to 30 %, "
+                "CO2 slug x<640 um, Ca=1e-4, theta=150 deg through CO2, dt_vd=0.1 dt_CFL, N from Brackbill")
+    elif name == "micromodel_2d":
+        c = inputs.micromodel_2d()
+        desc = "2D random-disc micromodel 2048x1024 over 4x2 mm, porosity 0.5, Ca=1e-5, dt_vd=0.1 dt_CFL"
+    elif name == "bubble_2d":
+        c = inputs.channel_bubble_2d()
+        c.params["precision"] = inputs.PREC_FP64
+        desc = "2D bubble channel 128x16 over 800x100 um, Ca=1e-3, FP64, dt_vd=0.29 dt_CFL (N=50)"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return c, desc
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of the profiled kernel classes
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(kid: int, c, es: int) -> float:
+    p = c.params
+    d = p["dim"]
+    n = c.solid.size
+    nf = (p["nx"] + 1) * p["ny"] * (p["nz"] if d == 3 else 1) + p["nx"] * (p["ny"] + 1) * (p["nz"] if d == 3 else 1)
+    if d == 3:
+        nf += p["nx"] * p["ny"] * (p["nz"] + 1)
+    if kid == 0:   # RB-GS half sweep: x (all) + b, diag, fluid (half) + face coeffs (each face once) + x write (half)
+        return n * (es + 0.5 * (2 * es + 1) + 0.5 * es) + nf * es
+    if kid == 1:   # operator apply + dot: p (8) read, Ap (8) write, info (4), face coeffs once
+        return n * (8 + 8 + 4) + nf * es
+    if kid == 2:   # HbyA: v, vold, hbya (d each), alpha, rA, G (d*d), info; phic faces once
+        return n * (es * (3 * d + 2 + d * d) + 4) + nf * es
+    if kid == 3:   # transport (3 kernels): low, ratio, update
+        low = n * (es + 4 + 3 * es) + 2 * nf * es
+        ratio = n * (4 * es + 4 + 2 * es)
+        upd = n * (4 * es + 4 + es) + 2 * nf * es
+        return low + ratio + upd
+    if kid == 4:   # MG residual: x, b, diag, fluid, res + face coeffs once
+        return n * (4 * es + 1) + nf * es
+    raise ValueError(kid)
+
+
+KID_NAMES = {0: "k_mg_rbgs (finest level, half sweep)", 1: "k_cg_apply_dot", 2: "k_momentum_H",
+             3: "k_transport_{low,ratio,update}", 4: "k_mg_residual (finest level)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        try:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        load = [r["sm"] for r in rows if r["power"] > 200.0] or [r["sm"] for r in rows]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm) on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(c, nx_crop: int, n_sub: int):
+    """FP64 oracle on an x-crop of the workload (same cells, first nx_crop
+    columns from the slug front), one drag step + n_sub relaxation sub-steps.
+    Returns (cell_updates, seconds, n_fluid, description)."""
+    import oracle
+    p = dict(c.params)
+    nx = p["nx"]
+    x0 = max(0, min(nx - nx_crop, int(0.4 * nx) - nx_crop // 2))
+    solid = np.ascontiguousarray(c.solid[..., x0:x0 + nx_crop])
+    a0 = np.ascontiguousarray(c.alpha0[..., x0:x0 + nx_crop])
+    solid = inputs.keep_outlet_connected(solid)
+    p["nx"] = nx_crop
+    p["precision"] = inputs.PREC_FP64
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(p, 0.1)
+    st = oracle.OracleState(p, solid, a0)
+    nfl = int((solid == 0).sum())
+    t0 = time.perf_counter()
+    st.drag_step(dt_vd)
+    st.relax(dt_vd / N, n_sub)
+    dt = time.perf_counter() - t0
+    desc = (f"oracle FP64, 1 thread, x-crop {nx_crop} of {nx} columns ({solid.shape} cells, {nfl} fluid), "
+            f"1 drag step + {n_sub} relaxation sub-steps")
+    return nfl * (1 + n_sub), dt, nfl, desc
+
+
+def run_reference(args, c, desc):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    nx_crop = 16 if c.params["dim"] == 3 else 128
+    cu_tot, t_tot = 0, 0.0
+    for _ in range(args.warmup):
+        oracle_sample(c, nx_crop, 1)
+    for _ in range(args.steps):
+        cu, t, nfl, sdesc = oracle_sample(c, nx_crop, 1)
+        cu_tot += cu
+        t_tot += t
+    v = cu_tot / t_tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="oscar", choices=["oscar", "reference"])
+    ap.add_argument("--workload", default="constriction_3d",
+                    choices=["constriction_3d", "micromodel_2d", "bubble_2d"])
+    ap.add_argument("--max-sub", type=int, default=0, help="cap on relaxation sub-steps per step (0 = N)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    c, desc = make_workload(args.workload)
+
+    if args.impl == "reference":
+        return run_reference(args, c, desc)
+
+    # CPU baseline first (before any CUDA context exists)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nx_crop = 16 if c.params["dim"] == 3 else 128
+        cu, t, nfl, sdesc = oracle_sample(c, nx_crop, 1)
+        cpu_baseline = {"value": cu / t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2105_10576_gb300 import oscar as ox
+
+    p = c.params
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"])
+    nsub = N if args.max_sub <= 0 else min(N, args.max_sub)
+    dt_cr = dt_vd / N
+    stream = torch.cuda.Stream()
+    sim = ox.Oscar(p, c.solid, c.alpha0, stream=stream.cuda_stream)
+    st0 = sim.stats()
+    nfluid = st0["n_fluid"]
+
+    def step():
+        sim.drag_step(dt_vd, strict=False)
+        return sim.relax(dt_cr, nsub, strict=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM -----------------------------
+    sim.profile(True)
+    sim.profile_read(0, reset=True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if \
+        os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    s_before = sim.stats()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    kfs = []
+    for _ in range(args.steps):
+        kfs.append(step()[1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s_after = sim.stats()
+    clk = clocks.stop()
+    prof = {k: sim.profile_read(k) for k in range(5)}
+    sim.profile(False)
+    cu = s_after["cell_updates"] - s_before["cell_updates"]
+    launches = s_after["kernel_launches"] - s_before["kernel_launches"]
+    if dist is not None:
+        t = torch.tensor([ms, float(cu), float(launches)], device="cuda", dtype=torch.float64)
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms, cu, launches = float(tmax[0]), float(t[1]), int(t[2])
+    value = cu / (ms / 1e3)
+
+    # ---- roofline of the dominant profiled kernel class --------------------
+    es = 8 if p["precision"] == inputs.PREC_FP64 else 4
+    kid = max(prof, key=lambda k: prof[k][0])
+    tot_ms, nl = prof[kid]
+    avg_s = (tot_ms / max(nl, 1)) / 1e3
+    ab = algorithmic_bytes(kid, c, es)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = ab / avg_s / 1e9 if avg_s > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": KID_NAMES[kid], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "avg_launch_us": avg_s * 1e6, "launches": nl,
+                "share_of_step": tot_ms / ms if ms > 0 else None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    # ---- end-to-end through the C ABI with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        host_alpha = sim.field(ox.FIELD_ALPHA)
+        h2d = host_alpha.nbytes
+        d2h = 0
+        cu0 = sim.stats()["cell_updates"]
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_field(ox.FIELD_ALPHA, host_alpha)
+            step()
+            host_alpha = sim.field(ox.FIELD_ALPHA)
+            ux = sim.field(ox.FIELD_U)
+            d2h = host_alpha.nbytes + ux.nbytes
+        t_e2e = time.perf_counter() - t0
+        cu_e2e = sim.stats()["cell_updates"] - cu0
+        e2e = {"value": cu_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        if dist is not None:
+            t = torch.tensor([t_e2e, float(cu_e2e)], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+            e2e["value"] = float(t[1]) / float(t[0])
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if p["precision"] == inputs.PREC_FP64 else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": desc, "cells": int(c.solid.size), "fluid_cells": int(nfluid),
+                           "N": int(N), "sub_steps_per_step": int(nsub), "k_f": kfs,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "working set larger than L2 (no flush needed)",
+                           "device_bytes": int(s_after["device_bytes"])},
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * oscar.h - C ABI of the GB300 (sm_103a) implementation of OSCAR, Operator
+ * Splitting with Capillary Relaxation (Maes & Menke, arXiv 2105.10576), on a
+ * uniform voxel grid with a solid mask.
+ *
+ * One handle holds one simulation instance: every field, face flux and
+ * multigrid level of it lives in device memory owned by the library. All
+ * arguments are plain host values or host pointers unless a name ends in
+ * "_device". Calls on one handle are ordered on the CUDA stream given at
+ * creation; calls that return host data wait for that stream with a bounded
+ * wait (OSCAR_E_TIMEOUT after 600 s). No call aborts the process or traps the
+ * device. Calls on one handle are not thread-safe; distinct handles are
+ * independent.
+ *
+ * Conventions (shared by every entry point):
+ *   - cells are indexed c = i + nx*(j + ny*k), x fastest; 2D grids have nz = 1;
+ *   - solid[c] = 1 marks a solid cell; fluid/solid faces and the y/z domain
+ *     boundaries are walls; x-min is the inlet, x-max the outlet (Section 3:
+ *     inlet with constant injected velocity, free outlet, no-slip walls);
+ *   - face arrays of direction a hold the faces on the low side of every cell
+ *     plus one extra layer: (nx+1)*ny*nz x-faces, nx*(ny+1)*nz y-faces,
+ *     nx*ny*(nz+1) z-faces, fluxes oriented along +a;
+ *   - alpha = 1 is phase 1 (rho1, mu1); theta_deg is measured through phase 1.
+ *
+ * Return codes: 0 on success, a negative OSCAR_E_* value otherwise. After
+ * OSCAR_E_CUDA the handle may only be destroyed.
+ */
+#ifndef OSCAR_H
+#define OSCAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OSCAR_OK 0
+#define OSCAR_E_INVALID_ARG (-1)
+#define OSCAR_E_OOM (-2)
+#define OSCAR_E_NOT_CONVERGED (-3)
+#define OSCAR_E_NAN (-4)
+#define OSCAR_E_TIMEOUT (-5)
+#define OSCAR_E_CUDA (-6)
+
+#define OSCAR_FP64 0  /* every field and solve in FP64 */
+#define OSCAR_MIXED 1 /* FP32 fields, stencils and V-cycles; FP64 CG vectors, dots, norms, sums */
+
+#define OSCAR_CONV_PRES_RESID 0 /* E_k: normalised initial residual of PISO corrector 1 (Section 3.2) */
+#define OSCAR_CONV_DU_MAX 1     /* max |u_cr^{k+1} - u_cr^k| / U_inlet */
+
+/* Field selectors for oscar_fields / oscar_set_field. */
+#define OSCAR_FIELD_ALPHA 0
+#define OSCAR_FIELD_P 1      /* p = p_vd + p_cr (Section 3.2 reconstruction) */
+#define OSCAR_FIELD_U 2      /* 2,3,4: u = u_vd + (1/N) sum_k u_cr^{n,k} */
+#define OSCAR_FIELD_U_VD 5   /* 5,6,7 */
+#define OSCAR_FIELD_U_CR 8   /* 8,9,10 */
+#define OSCAR_FIELD_P_VD 11
+#define OSCAR_FIELD_P_CR 12
+#define OSCAR_FIELD_KAPPA 13
+#define OSCAR_FIELD_PHI_VD 14 /* 14,15,16 (face arrays) */
+#define OSCAR_FIELD_PHI_CR 17 /* 17,18,19 (face arrays) */
+#define OSCAR_FIELD_NF 20     /* 20,21,22 face-normal component of the interface normal */
+
+/* Problem statement and numerical parameters (Section 3, problem statement;
+ * Sections 2.1-2.2 for the fluid model). Plain host struct, copied at
+ * creation. */
+typedef struct {
+    int dim;               /* 2 or 3 */
+    int nx, ny, nz;        /* cells per direction (nz = 1 in 2D) */
+    double hx, hy, hz;     /* cell size [m] */
+    double rho1, rho2;     /* densities [kg/m^3] of phase 1 (alpha = 1) and phase 2 */
+    double mu1, mu2;       /* viscosities [Pa s] */
+    double sigma;          /* interfacial tension [N/m] */
+    double theta_deg;      /* static contact angle through phase 1 [deg] */
+    double U_inlet;        /* injected velocity at x-min [m/s] */
+    double alpha_inlet;    /* alpha of the injected fluid */
+    int n_piso;            /* PISO correctors (3 in the paper, Section 2.2) */
+    int n_smooth;          /* smoothing passes of alpha before the normal (2) */
+    double c_alpha;        /* interface-compression coefficient (1) */
+    int conv_mode;         /* OSCAR_CONV_* */
+    double conv_tol;       /* relaxation tolerance (1e-4 for E_k in the paper) */
+    double cg_rtol;        /* pressure solve: stop at ||r||_2 <= cg_rtol ||b||_2 */
+    int cg_maxit;          /* pressure solve iteration cap */
+    int precision;         /* OSCAR_FP64 or OSCAR_MIXED */
+} oscar_params;
+
+typedef struct {
+    int k_f;                  /* sub-steps run in the last relaxation (Section 3.2) */
+    int N;                    /* sub-steps allowed in the last relaxation */
+    double E_last;            /* E_k of the last sub-step */
+    double dU_last;           /* max |u_cr^{k+1} - u_cr^k| / U_inlet of the last sub-step */
+    long long cg_iters_total; /* PCG iterations since creation */
+    int cg_iters_last;        /* PCG iterations of the last step or sub-step */
+    int mg_levels;            /* multigrid levels of the pressure preconditioner */
+    double phase_volume;      /* sum over fluid cells of alpha V (FP64) */
+    long long n_fluid;        /* fluid cells */
+    long long cell_updates;   /* fluid cells x (drag + relaxation + standard steps) since creation */
+    size_t device_bytes;      /* device memory held by the handle */
+    long long kernel_launches; /* CUDA kernels launched by this handle since creation */
+} oscar_stats_t;
+
+typedef struct oscar_instance *oscar_handle;
+
+/* Time-step control (Section 2.2, CFL and Brackbill limits; Section 3.2, N).
+ * out[0] = dt_CFL = hx / U_inlet; out[1] = dt_B = sqrt(rho_bar h_min^3 / (2 pi sigma)),
+ * rho_bar = (rho1 + rho2)/2, h_min the smallest spacing; out[2] = dt_vd = c_cfl dt_CFL;
+ * out[3] = N, the smallest integer with dt_vd / N < dt_B. Host arithmetic only. */
+int oscar_timesteps(const oscar_params *p, double c_cfl, double out[4]);
+
+/* Create an instance. solid: host uint8[ncell]; alpha0: host double[ncell]
+ * (values in solid cells ignored). stream: a cudaStream_t (NULL = default
+ * stream). Velocities, pressures and fluxes start at zero (fluid at rest).
+ * Allocates all device memory of the instance. */
+int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alpha0, void *stream,
+                 oscar_handle *out);
+
+/* Viscous-drag step (Section 3.1, Eqs. VOFd, NSE1d, md): alpha^n -> alpha*
+ * with u_vd^n; momentum for u_vd with convecting velocity u_vd^n + u_cr^n,
+ * no surface tension, inlet velocity U_inlet, outlet p_vd = 0; PISO. */
+int oscar_drag_step(oscar_handle h, double dt_vd);
+
+/* Capillary relaxation (Section 3.2, Eqs. VOFc, NSEc, mc): up to N sub-steps of
+ * dt_cr, each an explicit alpha step with u_cr, the CSF force of the new alpha,
+ * and PISO for u_cr (zero at the inlet) with convecting velocity u_vd + u_cr;
+ * stops after sub-step k_f when the test value (E_k or max |du_cr|/U) is
+ * below conv_tol, or at k_f = N. Then u = u_vd + (1/N) sum_{k<=k_f} u_cr^{n,k}.
+ * k_f_out and test_out (may be NULL) receive k_f and the last test value. */
+int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_out);
+
+/* Standard time-stepping (Section 2.2): one explicit alpha step with u^n, then
+ * PISO with surface tension and the inlet velocity. In this mode the drag
+ * fields (u_vd, p_vd, phi_vd) hold u, p, phi and the relaxation fields stay 0. */
+int oscar_standard_step(oscar_handle h, double dt);
+
+/* Copy one field to host memory (double). n must equal the field's length
+ * (ncell, or the face count of its direction). Waits for the stream. */
+int oscar_fields(oscar_handle h, int which, double *host_out, size_t n);
+
+/* Same, into device memory (double) on the handle's stream; does not wait. */
+int oscar_fields_device(oscar_handle h, int which, double *dev_out, size_t n);
+
+/* Overwrite one state field from host memory (double): ALPHA (recomputes the
+ * interface normals and curvature), U_VD, U_CR, P_VD (also selected by P),
+ * P_CR, PHI_VD, PHI_CR. Waits for the stream. */
+int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n);
+
+/* Statistics of the instance (waits for the stream). */
+int oscar_stats(oscar_handle h, oscar_stats_t *out);
+
+/* Release all device memory of the instance. */
+int oscar_destroy(oscar_handle h);
+
+/* Static string for a return code. */
+const char *oscar_strerror(int code);
+
+/* Kernel-class timing with CUDA events on the handle's stream (measurement
+ * support, not part of the method). enable = 1 starts recording every launch
+ * of the classes below (events from a fixed pool; records past its capacity
+ * are dropped and counted), 0 stops. oscar_profile_read waits for the stream
+ * and returns, for class kid, the summed device time [ms] and the number of
+ * launches recorded since the last reset; reset = 1 clears all classes. */
+#define OSCAR_KID_RBGS0 0      /* red-black Gauss-Seidel half-sweep, finest level */
+#define OSCAR_KID_CG_APPLY 1   /* pressure operator apply fused with p.Ap */
+#define OSCAR_KID_MOMENTUM 2   /* HbyA evaluation */
+#define OSCAR_KID_TRANSPORT 3  /* the three alpha-transport kernels of one step */
+#define OSCAR_KID_RESID0 4     /* multigrid residual, finest level */
+#define OSCAR_KID_COUNT 5
+int oscar_profile(oscar_handle h, int enable);
+int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OSCAR_H */

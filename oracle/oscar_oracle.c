@@ -577,9 +577,11 @@ static double vel_face_value(const or_grid *g, double *const v[3], const double 
 }
 
 /* HbyA = H / A for the current velocity iterate v: H holds the old-time term,
- * the explicit neighbour part of the viscous Laplacian, the linear-upwind
- * convection (advective form) and the explicit transpose viscous term
- * div(mu grad v^T). G receives the Gauss gradients G[comp][dir] of v. */
+ * the neighbour part of the viscous Laplacian, the neighbour (inflow) part of
+ * the upwind convection, the explicit linear-upwind correction (advective
+ * form) and the explicit transpose viscous term div(mu grad v^T); the
+ * outflow part of upwind convection sits in A (implicit). G receives the
+ * Gauss gradients G[comp][dir] of v. */
 static void momentum_HbyA(const or_grid *g, double *const v[3], double *const v_old[3],
                           double *const phic[3], const double *rho_n, const double *mu_n,
                           const double *rA, const double vin[3], double dt,
@@ -598,7 +600,7 @@ static void momentum_HbyA(const or_grid *g, double *const v[3], double *const v_
         if (g->solid[c]) continue;
         for (int comp = 0; comp < D; ++comp) {
             double Hc = rho_n[c] * v_old[comp][c] / dt;
-            double lap = 0.0, conv = 0.0, tr = 0.0;
+            double lap = 0.0, conv = 0.0, tr = 0.0, inflow = 0.0;
             for (int a = 0; a < D; ++a)
                 for (int s = 0; s < 2; ++s) {
                     int f, nb;
@@ -607,25 +609,30 @@ static void momentum_HbyA(const or_grid *g, double *const v[3], double *const v_
                     if (t == OR_F_INTERIOR) {
                         double muf = 0.5 * (mu_n[c] + mu_n[nb]);
                         lap += muf * g->S[a] / g->h[a] * v[comp][nb];
-                        /* linear-upwind face value for the convecting flux (oriented +a) */
+                        /* upwind (implicit part) and linear-upwind (explicit correction) face
+                         * values for the convecting flux phic (oriented +a) */
                         int L = s ? c : nb, Hh = s ? nb : c;
-                        double vf;
-                        if (phic[a][f] >= 0.0) vf = v[comp][L] + 0.5 * g->h[a] * G[comp][a][L];
-                        else vf = v[comp][Hh] - 0.5 * g->h[a] * G[comp][a][Hh];
-                        conv += sg * phic[a][f] * (vf - v[comp][c]);
+                        double vf, vu;
+                        if (phic[a][f] >= 0.0) { vu = v[comp][L]; vf = vu + 0.5 * g->h[a] * G[comp][a][L]; }
+                        else { vu = v[comp][Hh]; vf = vu - 0.5 * g->h[a] * G[comp][a][Hh]; }
+                        double fo = sg * phic[a][f];       /* outward flux of cell c */
+                        if (fo < 0.0) inflow += -fo * v[comp][nb];
+                        conv += fo * (vf - vu);
                         double dvdx = 0.5 * (G[a][comp][c] + G[a][comp][nb]);
                         tr += sg * muf * g->S[a] * dvdx;
                     } else if (t == OR_F_WALL) {
                         tr += sg * mu_n[c] * g->S[a] * G[a][comp][c];
                     } else if (t == OR_F_INLET) {
                         lap += mu_n[c] * g->S[a] / (0.5 * g->h[a]) * vin[comp];
-                        conv += sg * phic[a][f] * (vin[comp] - v[comp][c]);
+                        double fo = sg * phic[a][f];
+                        if (fo < 0.0) inflow += -fo * vin[comp];
+                        else conv += fo * (vin[comp] - v[comp][c]);
                         tr += sg * mu_n[c] * g->S[a] * G[a][comp][c];
                     } else if (t == OR_F_OUTLET) {
                         tr += sg * mu_n[c] * g->S[a] * G[a][comp][c];
                     }
                 }
-            Hc += (lap - rho_n[c] * conv + tr) / g->V;
+            Hc += (lap + rho_n[c] * (inflow - conv) + tr) / g->V;
             HbyA[comp][c] = rA[c] * Hc;
         }
     }
@@ -652,18 +659,23 @@ static void piso(const or_grid *g, const or_params *P,
         rho_n[c] = mix_rho(P, alpha_new[c]);
         mu_n[c] = mix_mu(P, alpha_new[c]);
     }
-    /* diagonal A = rho_new/dt + (1/V) sum mu_f S/delta over interior, wall and inlet faces */
+    /* diagonal A = rho_new/dt + (1/V) sum mu_f S/delta over interior, wall and inlet faces
+     * + (rho_new/V) sum of the inflow fluxes (implicit upwind part of convection) */
     for (int c = 0; c < nc; ++c) {
         if (g->solid[c]) continue;
-        double acc = 0.0;
+        double acc = 0.0, cin = 0.0;
         for (int a = 0; a < D; ++a)
             for (int s = 0; s < 2; ++s) {
                 int f, nb;
                 int t = cell_face(g, c, a, s, &f, &nb);
                 if (t == OR_F_INTERIOR) acc += 0.5 * (mu_n[c] + mu_n[nb]) * g->S[a] / g->h[a];
                 else if (t == OR_F_WALL || t == OR_F_INLET) acc += mu_n[c] * g->S[a] / (0.5 * g->h[a]);
+                if (t == OR_F_INTERIOR || t == OR_F_INLET) {
+                    double fo = (s ? 1.0 : -1.0) * phic[a][f];
+                    if (fo < 0.0) cin += -fo;
+                }
             }
-        rA[c] = 1.0 / (rho_n[c] / dt + acc / g->V);
+        rA[c] = 1.0 / (rho_n[c] / dt + (acc + rho_n[c] * cin) / g->V);
     }
     /* face coefficients of the pressure operator, CSF face forces */
     for (int a = 0; a < D; ++a) {
@@ -1063,15 +1075,19 @@ void or_stage_momentum(const or_params *P, const uint8_t *solid,
     }
     for (int c = 0; c < nc; ++c) {
         if (g.solid[c]) continue;
-        double acc = 0.0;
+        double acc = 0.0, cin = 0.0;
         for (int a = 0; a < D; ++a)
             for (int s = 0; s < 2; ++s) {
                 int f, nb;
                 int t = cell_face(&g, c, a, s, &f, &nb);
                 if (t == OR_F_INTERIOR) acc += 0.5 * (mu_n[c] + mu_n[nb]) * g.S[a] / g.h[a];
                 else if (t == OR_F_WALL || t == OR_F_INLET) acc += mu_n[c] * g.S[a] / (0.5 * g.h[a]);
+                if (t == OR_F_INTERIOR || t == OR_F_INLET) {
+                    double fo = (s ? 1.0 : -1.0) * pc[a][f];
+                    if (fo < 0.0) cin += -fo;
+                }
             }
-        rA_out[c] = 1.0 / (rho_n[c] / dt + acc / g.V);
+        rA_out[c] = 1.0 / (rho_n[c] / dt + (acc + rho_n[c] * cin) / g.V);
     }
     momentum_HbyA(&g, v, vo, pc, rho_n, mu_n, rA_out, vin, dt, G, HbyA);
     free(rho_n); free(mu_n);

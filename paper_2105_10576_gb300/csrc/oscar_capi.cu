@@ -1,0 +1,438 @@
+// C ABI of the OSCAR library (declared in include/oscar.h): instance
+// creation, memory layout, multigrid hierarchy and dispatch to the FP64 or
+// mixed-precision solver.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <new>
+#include <vector>
+
+#include "oscar_internal.h"
+
+struct oscar_instance {
+    oscar::Instance I;
+};
+
+namespace oscar {
+
+int sync_bounded(cudaStream_t s, double timeout_sec) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (unsigned long it = 0;; ++it) {
+        cudaError_t e = cudaStreamQuery(s);
+        if (e == cudaSuccess) return 0;
+        if (e != cudaErrorNotReady) {
+            fprintf(stderr, "oscar: stream error %s\n", cudaGetErrorString(e));
+            return OSCAR_E_CUDA;
+        }
+        if ((it & 1023) == 0) {
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > timeout_sec) return OSCAR_E_TIMEOUT;
+        }
+    }
+}
+
+int prof_begin(Instance &I, int kid) {
+    Profiler *P = I.prof;
+    if (!P || !P->enabled) return -1;
+    if (P->n >= kProfPool) {
+        // drain: wait for the recorded launches and accumulate their times
+        if (sync_bounded(I.stream, kSyncTimeoutSec)) { P->dropped++; return -1; }
+        for (int s = 0; s < P->n; ++s) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, P->ev0[s], P->ev1[s]) == cudaSuccess) {
+                P->total_ms[P->kid[s]] += ms;
+                P->launches[P->kid[s]] += 1;
+            } else {
+                cudaGetLastError();
+                P->dropped++;
+            }
+        }
+        P->n = 0;
+    }
+    int s = P->n++;
+    P->kid[s] = kid;
+    cudaEventRecord(P->ev0[s], I.stream);
+    return s;
+}
+
+void prof_end(Instance &I, int slot) {
+    if (slot >= 0) cudaEventRecord(I.prof->ev1[slot], I.stream);
+}
+
+size_t field_len(const Instance &I, int which) {
+    if (which >= 0 && which <= OSCAR_FIELD_KAPPA) return (size_t)I.g.ncell;
+    if (which >= OSCAR_FIELD_PHI_VD && which <= OSCAR_FIELD_NF + 2) return (size_t)I.g.nf[(which - OSCAR_FIELD_PHI_VD) % 3];
+    return 0;
+}
+
+static GridH make_grid(int dim, int nx, int ny, int nz, double hx, double hy, double hz) {
+    GridH g;
+    g.dim = dim;
+    g.nx = nx; g.ny = ny; g.nz = dim == 3 ? nz : 1;
+    g.ncell = g.nx * g.ny * g.nz;
+    g.nf[0] = (g.nx + 1) * g.ny * g.nz;
+    g.nf[1] = g.nx * (g.ny + 1) * g.nz;
+    g.nf[2] = g.nx * g.ny * (g.nz + 1);
+    g.h[0] = hx; g.h[1] = hy; g.h[2] = hz;
+    g.V = 1.0;
+    for (int a = 0; a < dim; ++a) g.V *= g.h[a];
+    for (int a = 0; a < 3; ++a) g.S[a] = a < dim ? g.V / g.h[a] : 0.0;
+    return g;
+}
+
+// Coarsening: halve every direction whose spacing is below twice the smallest
+// spacing (semi-coarsening of the strongly coupled directions on anisotropic
+// cells), until at most 64 cells remain.
+static void build_hierarchy(Instance &I) {
+    I.nlev = 1;
+    I.lev[0].g = I.g;
+    while (I.nlev < kMaxLevels) {
+        GridH &g = I.lev[I.nlev - 1].g;
+        int *r = I.lev[I.nlev - 1].r;
+        r[0] = r[1] = r[2] = 1;
+        if (g.ncell <= 64) break;
+        int n[3] = {g.nx, g.ny, g.nz};
+        double hmin = 1e300;
+        for (int a = 0; a < g.dim; ++a)
+            if (n[a] > 1 && g.h[a] < hmin) hmin = g.h[a];
+        bool any = false;
+        for (int a = 0; a < g.dim; ++a)
+            if (n[a] > 1 && g.h[a] < 2.0 * hmin) { r[a] = 2; any = true; }
+        if (!any) break;
+        GridH c = make_grid(g.dim, (g.nx + r[0] - 1) / r[0], (g.ny + r[1] - 1) / r[1], (g.nz + r[2] - 1) / r[2],
+                            g.h[0] * r[0], g.h[1] * r[1], g.h[2] * r[2]);
+        I.lev[I.nlev].g = c;
+        I.lev[I.nlev].r[0] = I.lev[I.nlev].r[1] = I.lev[I.nlev].r[2] = 1;
+        ++I.nlev;
+    }
+}
+
+struct Carver {
+    char *base;
+    size_t off;
+    bool dry;
+    void *take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        void *p = dry ? nullptr : base + off;
+        off += bytes;
+        return p;
+    }
+};
+
+static void carve(Instance &I, Carver &C) {
+    size_t es = I.prec == OSCAR_FP64 ? sizeof(double) : sizeof(float);
+    size_t nc = I.g.ncell;
+    I.info = (uint32_t *)C.take(nc * sizeof(uint32_t));
+    void **cells[] = {&I.alpha, &I.alpha_new, &I.alpha_s, &I.alpha_tmp, &I.kappa, &I.aL, &I.Pp, &I.Pm, &I.Rp, &I.Rm, &I.rA};
+    for (void **p : cells) *p = C.take(nc * es);
+    for (int a = 0; a < 3; ++a) {
+        I.hbya[a] = C.take(nc * es);
+        I.vold[a] = C.take(nc * es);
+        I.u_vd[a] = C.take(nc * es);
+        I.u_cr[a] = C.take(nc * es);
+        I.u_sum[a] = (double *)C.take(nc * sizeof(double));
+    }
+    for (int q = 0; q < 9; ++q) I.G[q] = C.take(nc * es);
+    I.p_vd = (double *)C.take(nc * sizeof(double));
+    I.p_cr = (double *)C.take(nc * sizeof(double));
+    I.cg_b = (double *)C.take(nc * sizeof(double));
+    I.cg_r = (double *)C.take(nc * sizeof(double));
+    I.cg_z = (double *)C.take(nc * sizeof(double));
+    I.cg_p = (double *)C.take(nc * sizeof(double));
+    I.cg_Ap = (double *)C.take(nc * sizeof(double));
+    for (int a = 0; a < 3; ++a) {
+        size_t nf = I.g.nf[a];
+        I.nf[a] = C.take(nf * es);
+        I.phi_vd[a] = C.take(nf * es);
+        I.phi_cr[a] = C.take(nf * es);
+        I.phic[a] = C.take(nf * es);
+        I.phis[a] = C.take(nf * es);
+        I.fst[a] = C.take(nf * es);
+    }
+    for (int l = 0; l < I.nlev; ++l) {
+        Level &L = I.lev[l];
+        size_t n = L.g.ncell;
+        L.fluid = (uint8_t *)C.take(n);
+        for (int a = 0; a < 3; ++a) L.c[a] = C.take((size_t)L.g.nf[a] * es);
+        L.diag = C.take(n * es);
+        L.x = C.take(n * es);
+        L.b = C.take(n * es);
+        L.res = C.take(n * es);
+    }
+    I.stage_dev = (double *)C.take(I.stage_len * sizeof(double));
+    I.partials = (double *)C.take((size_t)kRedSlots * kRedBlocks * sizeof(double));
+    I.scal = (double *)C.take(S_COUNT * sizeof(double));
+}
+
+static int validate(const oscar_params *p) {
+    if (!p) return OSCAR_E_INVALID_ARG;
+    if (p->dim != 2 && p->dim != 3) return OSCAR_E_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || (p->dim == 3 && p->nz < 1)) return OSCAR_E_INVALID_ARG;
+    double ncell = (double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1);
+    double nface = (double)(p->nx + 1) * p->ny * (p->dim == 3 ? p->nz + 1 : 1) * 2.0;
+    if (ncell > 2.0e9 || nface > 2.0e9) return OSCAR_E_INVALID_ARG;
+    if (!(p->hx > 0) || !(p->hy > 0) || (p->dim == 3 && !(p->hz > 0))) return OSCAR_E_INVALID_ARG;
+    if (!(p->rho1 > 0) || !(p->rho2 > 0) || p->mu1 < 0 || p->mu2 < 0 || p->sigma < 0) return OSCAR_E_INVALID_ARG;
+    if (p->n_piso < 1 || p->n_smooth < 0 || p->cg_maxit < 1 || !(p->cg_rtol > 0)) return OSCAR_E_INVALID_ARG;
+    if (p->precision != OSCAR_FP64 && p->precision != OSCAR_MIXED) return OSCAR_E_INVALID_ARG;
+    if (p->conv_mode != OSCAR_CONV_PRES_RESID && p->conv_mode != OSCAR_CONV_DU_MAX) return OSCAR_E_INVALID_ARG;
+    return 0;
+}
+
+}  // namespace oscar
+
+using namespace oscar;
+
+extern "C" {
+
+int oscar_timesteps(const oscar_params *p, double c_cfl, double out[4]) {
+    if (!p || !out || !(p->U_inlet > 0) || !(p->sigma > 0) || !(c_cfl > 0)) return OSCAR_E_INVALID_ARG;
+    double hmin = p->hx;
+    if (p->hy < hmin) hmin = p->hy;
+    if (p->dim == 3 && p->hz < hmin) hmin = p->hz;
+    double dt_cfl = p->hx / p->U_inlet;
+    double rho_bar = 0.5 * (p->rho1 + p->rho2);
+    double dt_b = sqrt(rho_bar * hmin * hmin * hmin / (2.0 * M_PI * p->sigma));
+    double dt_vd = c_cfl * dt_cfl;
+    out[0] = dt_cfl;
+    out[1] = dt_b;
+    out[2] = dt_vd;
+    out[3] = floor(dt_vd / dt_b) + 1.0;
+    return 0;
+}
+
+const char *oscar_strerror(int code) {
+    switch (code) {
+        case OSCAR_OK: return "ok";
+        case OSCAR_E_INVALID_ARG: return "invalid argument";
+        case OSCAR_E_OOM: return "out of device memory";
+        case OSCAR_E_NOT_CONVERGED: return "pressure solve hit its iteration cap";
+        case OSCAR_E_NAN: return "non-finite value in the solution";
+        case OSCAR_E_TIMEOUT: return "bounded wait for the stream timed out";
+        case OSCAR_E_CUDA: return "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alpha0, void *stream,
+                 oscar_handle *out) {
+    if (!out) return OSCAR_E_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (!solid || !alpha0) return OSCAR_E_INVALID_ARG;
+    oscar_instance *H = new (std::nothrow) oscar_instance();
+    if (!H) return OSCAR_E_OOM;
+    Instance &I = H->I;
+    memset(&I, 0, sizeof(Instance));
+    I.P = *p;
+    I.prec = p->precision;
+    I.stream = (cudaStream_t)stream;
+    I.g = make_grid(p->dim, p->nx, p->ny, p->nz, p->hx, p->hy, p->hz);
+    I.cos_theta = cos(p->theta_deg * M_PI / 180.0);
+    I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
+    I.last_N = 1;
+    I.mg_nu = 2;
+    I.mg_coarse_sweeps = 8;
+    long long nf = 0;
+    for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
+    I.n_fluid = nf;
+    if (nf == 0) { delete H; return OSCAR_E_INVALID_ARG; }
+    build_hierarchy(I);
+    size_t stage = I.g.ncell;
+    for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];
+    I.stage_len = stage;
+    Carver dry{nullptr, 0, true};
+    carve(I, dry);
+    I.arena_bytes = dry.off + 256;
+    if (cudaMalloc(&I.arena, I.arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete H;
+        return OSCAR_E_OOM;
+    }
+    Carver wet{(char *)I.arena, 0, false};
+    carve(I, wet);
+    if (cudaMallocHost(&I.scal_host, S_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&I.stage_host, stage * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(I.arena);
+        delete H;
+        return OSCAR_E_OOM;
+    }
+    if (cudaMemsetAsync(I.arena, 0, I.arena_bytes, I.stream) != cudaSuccess) { oscar_destroy(H); return OSCAR_E_CUDA; }
+    // upload the mask and alpha0 through a temporary device buffer
+    void *tmp = nullptr;
+    size_t tbytes = (size_t)I.g.ncell * (sizeof(double) + 1);
+    if (cudaMalloc(&tmp, tbytes) != cudaSuccess) { cudaGetLastError(); oscar_destroy(H); return OSCAR_E_OOM; }
+    double *a0d = (double *)tmp;
+    uint8_t *sd = (uint8_t *)(a0d + I.g.ncell);
+    cudaMemcpyAsync(a0d, alpha0, (size_t)I.g.ncell * sizeof(double), cudaMemcpyHostToDevice, I.stream);
+    cudaMemcpyAsync(sd, solid, (size_t)I.g.ncell, cudaMemcpyHostToDevice, I.stream);
+    rc = I.prec == OSCAR_FP64 ? Solver<double>::setup(I, sd, a0d) : Solver<float>::setup(I, sd, a0d);
+    int rc2 = sync_bounded(I.stream, kSyncTimeoutSec);
+    cudaFree(tmp);
+    if (rc || rc2) { oscar_destroy(H); return rc ? rc : rc2; }
+    *out = H;
+    return 0;
+}
+
+int oscar_destroy(oscar_handle h) {
+    if (!h) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.arena) {
+        sync_bounded(I.stream, kSyncTimeoutSec);
+        cudaFree(I.arena);
+    }
+    if (I.prof) {
+        if (I.prof->created)
+            for (int s = 0; s < kProfPool; ++s) { cudaEventDestroy(I.prof->ev0[s]); cudaEventDestroy(I.prof->ev1[s]); }
+        delete I.prof;
+    }
+    if (I.scal_host) cudaFreeHost(I.scal_host);
+    if (I.stage_host) cudaFreeHost(I.stage_host);
+    delete h;
+    return 0;
+}
+
+int oscar_drag_step(oscar_handle h, double dt_vd) {
+    if (!h || !(dt_vd > 0)) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    return I.prec == OSCAR_FP64 ? Solver<double>::drag_step(I, dt_vd) : Solver<float>::drag_step(I, dt_vd);
+}
+
+int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_out) {
+    if (!h || !(dt_cr > 0) || N < 1) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.P.conv_mode == OSCAR_CONV_DU_MAX && !(I.P.U_inlet > 0)) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::relax(I, dt_cr, N, k_f_out, test_out)
+                                : Solver<float>::relax(I, dt_cr, N, k_f_out, test_out);
+}
+
+int oscar_standard_step(oscar_handle h, double dt) {
+    if (!h || !(dt > 0)) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    return I.prec == OSCAR_FP64 ? Solver<double>::standard_step(I, dt) : Solver<float>::standard_step(I, dt);
+}
+
+int oscar_fields_device(oscar_handle h, int which, double *dev_out, size_t n) {
+    if (!h || !dev_out) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    size_t len = field_len(I, which);
+    if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::field_to_device(I, which, dev_out, n)
+                                : Solver<float>::field_to_device(I, which, dev_out, n);
+}
+
+int oscar_fields(oscar_handle h, int which, double *host_out, size_t n) {
+    if (!h || !host_out) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    size_t len = field_len(I, which);
+    if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
+    int rc = I.prec == OSCAR_FP64 ? Solver<double>::field_to_device(I, which, I.stage_dev, len)
+                                  : Solver<float>::field_to_device(I, which, I.stage_dev, len);
+    if (!rc && cudaMemcpyAsync(I.stage_host, I.stage_dev, len * sizeof(double), cudaMemcpyDeviceToHost, I.stream) !=
+                   cudaSuccess)
+        rc = OSCAR_E_CUDA;
+    int rc2 = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    memcpy(host_out, I.stage_host, len * sizeof(double));
+    return 0;
+}
+
+int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n) {
+    if (!h || !host_in) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    size_t len = field_len(I, which);
+    if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    memcpy(I.stage_host, host_in, len * sizeof(double));
+    if (cudaMemcpyAsync(I.stage_dev, I.stage_host, len * sizeof(double), cudaMemcpyHostToDevice, I.stream) !=
+        cudaSuccess)
+        return OSCAR_E_CUDA;
+    rc = I.prec == OSCAR_FP64 ? Solver<double>::field_from_device(I, which, I.stage_dev, len)
+                              : Solver<float>::field_from_device(I, which, I.stage_dev, len);
+    int rc2 = sync_bounded(I.stream, kSyncTimeoutSec);
+    return rc ? rc : rc2;
+}
+
+int oscar_stats(oscar_handle h, oscar_stats_t *out) {
+    if (!h || !out) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    double vol = 0.0;
+    int rc = I.prec == OSCAR_FP64 ? Solver<double>::phase_volume(I, &vol) : Solver<float>::phase_volume(I, &vol);
+    if (rc) return rc;
+    out->k_f = I.last_kf;
+    out->N = I.last_N;
+    out->E_last = I.last_E;
+    out->dU_last = I.last_dU;
+    out->cg_iters_total = I.cg_iters_total;
+    out->cg_iters_last = I.cg_iters_last;
+    out->mg_levels = I.nlev;
+    out->phase_volume = vol;
+    out->n_fluid = I.n_fluid;
+    out->cell_updates = I.cell_updates;
+    out->device_bytes = I.arena_bytes;
+    out->kernel_launches = I.nlaunch;
+    return 0;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int oscar_profile(oscar_handle h, int enable) {
+    if (!h) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (!I.prof) {
+        I.prof = new (std::nothrow) Profiler();
+        if (!I.prof) return OSCAR_E_OOM;
+        memset(I.prof, 0, sizeof(Profiler));
+    }
+    if (enable && !I.prof->created) {
+        for (int s = 0; s < kProfPool; ++s) {
+            if (cudaEventCreate(&I.prof->ev0[s]) != cudaSuccess || cudaEventCreate(&I.prof->ev1[s]) != cudaSuccess)
+                return OSCAR_E_CUDA;
+        }
+        I.prof->created = 1;
+    }
+    I.prof->enabled = enable ? 1 : 0;
+    return 0;
+}
+
+int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset) {
+    if (!h || kid < 0 || kid >= OSCAR_KID_COUNT) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    Profiler *P = I.prof;
+    if (!P) {
+        if (total_ms) *total_ms = 0.0;
+        if (launches) *launches = 0;
+        return 0;
+    }
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    for (int s = 0; s < P->n; ++s) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->ev0[s], P->ev1[s]) == cudaSuccess) {
+            P->total_ms[P->kid[s]] += ms;
+            P->launches[P->kid[s]] += 1;
+        } else {
+            cudaGetLastError();
+            P->dropped++;
+        }
+    }
+    P->n = 0;
+    if (total_ms) *total_ms = P->total_ms[kid];
+    if (launches) *launches = P->launches[kid];
+    if (reset) {
+        for (int k = 0; k < OSCAR_KID_COUNT; ++k) { P->total_ms[k] = 0.0; P->launches[k] = 0; }
+        P->dropped = 0;
+    }
+    return 0;
+}
+
+}  // extern "C"

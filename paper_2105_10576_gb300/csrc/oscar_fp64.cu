@@ -1,0 +1,5 @@
+// FP64 path: every field, stencil and multigrid level in double.
+#include "oscar_kernels.cuh"
+namespace oscar {
+template struct Solver<double>;
+}

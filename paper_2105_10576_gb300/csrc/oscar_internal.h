@@ -1,0 +1,115 @@
+// Host-side instance layout shared by the C-ABI unit and the per-precision
+// solver units. Device code lives in oscar_kernels.cuh.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <vector>
+
+#include "../../include/oscar.h"
+
+namespace oscar {
+
+constexpr int kMaxLevels = 24;
+constexpr int kRedBlocks = 1216;      // 152 SMs x 8: fixed grid of every reduction (deterministic order)
+constexpr int kRedSlots = 16;         // partial-sum slots
+constexpr double kSyncTimeoutSec = 600.0;
+
+// Scalar slots in the device scalar array (double).
+enum Slot {
+    S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_R0, S_TMP, S_COUNT
+};
+
+struct GridH {
+    int dim, nx, ny, nz, ncell;
+    int nf[3];
+    double h[3], S[3], V;
+};
+
+struct Level {
+    GridH g;
+    int r[3];            // coarsening ratio to the next level (1 or 2 per direction)
+    uint8_t *fluid;      // level >= 1: any fine child fluid
+    void *c[3];          // face coefficients (T)
+    void *diag;          // T
+    void *x, *b, *res;   // T
+};
+
+// Optional kernel-class timing (events recorded around selected launches).
+constexpr int kProfPool = 8192;
+struct Profiler {
+    int enabled;
+    int n;                       // events pairs in use
+    long long dropped;
+    int kid[kProfPool];
+    cudaEvent_t ev0[kProfPool], ev1[kProfPool];
+    double total_ms[OSCAR_KID_COUNT];
+    long long launches[OSCAR_KID_COUNT];
+    int created;
+};
+
+// Device memory of one instance; element type T (double or float) is fixed by
+// the precision chosen at creation. CG vectors and accumulators are double.
+struct Instance {
+    oscar_params P;
+    GridH g;
+    cudaStream_t stream;
+    int prec;
+    long long n_fluid;
+    double cos_theta, deltaN;
+
+    // arena
+    void *arena;
+    size_t arena_bytes;
+
+    uint32_t *info;        // per-cell face types + fluid flag
+    // cell fields (T)
+    void *alpha, *alpha_new, *alpha_s, *alpha_tmp, *kappa;
+    void *aL, *Pp, *Pm, *Rp, *Rm;
+    void *rA;
+    void *hbya[3], *vold[3], *u_vd[3], *u_cr[3], *G[9];
+    // cell fields (double)
+    double *u_sum[3], *p_vd, *p_cr;
+    double *cg_b, *cg_r, *cg_z, *cg_p, *cg_Ap;
+    // face fields (T)
+    void *nf[3], *phi_vd[3], *phi_cr[3], *phic[3], *phis[3], *fst[3];
+    // multigrid (level 0 coefficients are the pressure operator's)
+    int nlev;
+    Level lev[kMaxLevels];
+    // reductions
+    double *partials;      // kRedSlots * kRedBlocks
+    double *scal;          // S_COUNT device scalars
+    double *scal_host;     // pinned mirror
+    double *stage_host;    // pinned staging for field transfers (max(ncell, faces) doubles)
+    double *stage_dev;     // device staging of the same length
+    size_t stage_len;
+
+    // statistics
+    int last_kf, last_N;
+    double last_E, last_dU;
+    long long cg_iters_total;
+    int cg_iters_last;
+    long long cell_updates;
+    int mg_nu, mg_coarse_sweeps;
+    long long nlaunch;     // kernels launched by this instance
+    Profiler *prof;
+};
+
+int prof_begin(Instance &I, int kid);
+void prof_end(Instance &I, int slot);
+
+// per-precision entry points (defined in oscar_kernels.cuh, instantiated twice)
+template <typename T> struct Solver {
+    static int setup(Instance &I, const uint8_t *solid_dev, const double *alpha0_dev);
+    static int drag_step(Instance &I, double dt);
+    static int relax(Instance &I, double dt, int N, int *kf, double *test);
+    static int standard_step(Instance &I, double dt);
+    static int field_to_device(Instance &I, int which, double *dst, size_t n);
+    static int field_from_device(Instance &I, int which, const double *src, size_t n);
+    static int phase_volume(Instance &I, double *out);
+};
+
+int sync_bounded(cudaStream_t s, double timeout_sec);
+size_t field_len(const Instance &I, int which);
+
+}  // namespace oscar

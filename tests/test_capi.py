@@ -1,0 +1,67 @@
+"""C-ABI library: builds for sm_103a, loads, exports every declared symbol,
+and its host-only entry points agree with the paper's formulas (no GPU)."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2105_10576_gb300 import build as gbuild
+from paper_2105_10576_gb300 import inputs, oscar
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return oscar.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "oscar.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(oscar_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_declares_binding_exports():
+    assert declared_symbols() == sorted(oscar.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_library_targets_sm103a(lib):
+    # the cubin is built for sm_103a only (checked through the build flags)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(gbuild.ARCH)
+
+
+def test_strerror(lib):
+    assert lib.oscar_strerror(0) == b"ok"
+    assert lib.oscar_strerror(-1) == b"invalid argument"
+
+
+@pytest.mark.parametrize("case", ["bubble", "constriction", "micromodel"])
+def test_timesteps_match_oracle(lib, case):
+    c = {"bubble": lambda: inputs.channel_bubble_2d(),
+         "constriction": lambda: inputs.constricted_channel_3d(nx=16, ny=8, nz=8),
+         "micromodel": lambda: inputs.micromodel_2d(nx=64, ny=32)}[case]()
+    cc = c.meta["c_cfl"]
+    a = oscar.oscar_timesteps(c.params, cc)
+    b = oracle.timesteps(c.params, cc)
+    for x, y in zip(a[:3], b[:3]):
+        assert x == pytest.approx(y, rel=1e-15)
+    assert a[3] == b[3]
+
+
+def test_create_rejects_bad_arguments(lib):
+    p = inputs.default_params(dim=4)
+    P = oscar.make_params(p)
+    h = C.c_void_p()
+    rc = lib.oscar_create(C.byref(P), None, None, None, C.byref(h))
+    assert rc == -1 and not h.value
+    assert lib.oscar_drag_step(None, 1.0) == -1
+    assert lib.oscar_relax(None, 1.0, 3, None, None) == -1

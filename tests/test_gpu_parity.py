@@ -1,0 +1,220 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+FP64 path: every state field (alpha, u, p, fluxes) within 1e-10 relative
+(max-norm) of the oracle. The interface normal n = g/(|g| + delta_N) and the
+curvature kappa = -div n amplify rounding-level differences of alpha by up to
+1/(h delta_N) = 1e8 where alpha is uniform (|g| << delta_N), so they are
+compared where they are well conditioned and act: kappa on the interface band
+0.01 < alpha < 0.99 (the CSF force sigma kappa grad alpha vanishes elsewhere).
+Mixed path: alpha within 1e-5 absolute, bubble velocity within 0.5 %.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_10576_gb300 import inputs
+from paper_2105_10576_gb300 import oscar as ox
+
+pytestmark = pytest.mark.gpu
+
+CELL_FIELDS = [("alpha", ox.FIELD_ALPHA, oracle.ALPHA), ("p", ox.FIELD_P, oracle.P),
+               ("ux", ox.FIELD_U, oracle.UX), ("uy", ox.FIELD_U + 1, oracle.UY),
+               ("uvdx", ox.FIELD_U_VD, oracle.UVDX), ("uvdy", ox.FIELD_U_VD + 1, oracle.UVDY),
+               ("ucrx", ox.FIELD_U_CR, oracle.UCRX), ("ucry", ox.FIELD_U_CR + 1, oracle.UCRY),
+               ("p_vd", ox.FIELD_P_VD, oracle.P_VD), ("p_cr", ox.FIELD_P_CR, oracle.P_CR),
+               ("kappa", ox.FIELD_KAPPA, oracle.KAPPA)]
+FACE_FIELDS = [("phi_vd_x", ox.FIELD_PHI_VD, oracle.PHI_VD), ("phi_vd_y", ox.FIELD_PHI_VD + 1, oracle.PHI_VD + 1),
+               ("phi_cr_x", ox.FIELD_PHI_CR, oracle.PHI_CR), ("phi_cr_y", ox.FIELD_PHI_CR + 1, oracle.PHI_CR + 1)]
+BAND = (0.01, 0.99)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def fields_for(dim):
+    cf = list(CELL_FIELDS)
+    ff = list(FACE_FIELDS)
+    if dim == 3:
+        cf += [("uz", ox.FIELD_U + 2, oracle.UZ), ("uvdz", ox.FIELD_U_VD + 2, oracle.UVDZ),
+               ("ucrz", ox.FIELD_U_CR + 2, oracle.UCRZ)]
+        ff += [("phi_vd_z", ox.FIELD_PHI_VD + 2, oracle.PHI_VD + 2),
+               ("phi_cr_z", ox.FIELD_PHI_CR + 2, oracle.PHI_CR + 2)]
+    return cf + ff
+
+
+def rel_err(x, y):
+    m = np.abs(y).max()
+    d = np.abs(x - y).max()
+    if m == 0.0:
+        return d
+    return d / m
+
+
+def compare(g, o, dim, tol, skip=()):
+    worst = {}
+    a_or = o.field(oracle.ALPHA)
+    band = (a_or > BAND[0]) & (a_or < BAND[1])
+    for name, wg, wo in fields_for(dim):
+        if name in skip:
+            continue
+        x, y = g.field(wg), o.field(wo)
+        if name == "kappa":
+            if not band.any():
+                continue
+            x, y = x[band], y[band]
+        e = rel_err(x, y)
+        worst[name] = e
+    bad = {k: v for k, v in worst.items() if not v <= tol}
+    assert not bad, f"fields over {tol}: {bad}"
+    return worst
+
+
+def run_oscar_pair(case, n_drag, n_sub, dt_vd, dt_cr, precision=inputs.PREC_FP64, N=None):
+    p = dict(case.params, precision=precision)
+    g = ox.Oscar(p, case.solid, case.alpha0)
+    o = oracle.OracleState(p, case.solid, case.alpha0)
+    kg, ko = [], []
+    for _ in range(n_drag):
+        g.drag_step(dt_vd)
+        o.drag_step(dt_vd)
+        _, k1, _ = g.relax(dt_cr, N or n_sub)
+        _, k2, _ = o.relax(dt_cr, N or n_sub)
+        kg.append(k1)
+        ko.append(k2)
+    return g, o, kg, ko
+
+
+SMALL = [("2d_ragged", lambda: inputs.random_small_case(1, 37, 13)),
+         ("2d_ragged_b", lambda: inputs.random_small_case(2, 23, 29, solid_frac=0.25)),
+         ("3d_ragged", lambda: inputs.random_small_case(3, 19, 11, nz=9, dim=3))]
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_fp64_oscar_small_matches_oracle(name, make):
+    c = make()
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)   # forced k_f = N
+    # the gaps between random solids carry up to ~8 U: c = 0.02 keeps the drag Courant number < 1
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, 0.02)
+    g, o, kg, ko = run_oscar_pair(c, 2, 4, dt_vd, 0.9 * dt_b)
+    assert kg == ko == [4, 4]
+    compare(g, o, c.params["dim"], 1e-10)
+    sg, so = g.stats(), o.stats()
+    assert sg["phase_volume"] == pytest.approx(so["phase_volume"], rel=1e-12)
+
+
+@pytest.mark.parametrize("name,make", SMALL)
+def test_fp64_standard_small_matches_oracle(name, make):
+    c = make()
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, 0.02)
+    g = ox.Oscar(c.params, c.solid, c.alpha0)
+    o = oracle.OracleState(c.params, c.solid, c.alpha0)
+    for _ in range(5):
+        g.standard_step(0.9 * dt_b)
+        o.standard_step(0.9 * dt_b)
+    compare(g, o, c.params["dim"], 1e-10, skip=("ucrx", "ucry", "ucrz", "phi_cr_x", "phi_cr_y", "phi_cr_z"))
+
+
+def test_fp64_early_exit_residual_matches_oracle():
+    """E_k (Section 3.2) per sub-step agrees, so both sides stop at the same k_f."""
+    c = inputs.random_small_case(4, 31, 17, sigma=0.0005)
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=5e-3)
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, 0.02)
+    g = ox.Oscar(c.params, c.solid, c.alpha0)
+    o = oracle.OracleState(c.params, c.solid, c.alpha0)
+    g.drag_step(dt_vd)
+    o.drag_step(dt_vd)
+    _, kg, Eg = g.relax(dt_vd / 40, 40)
+    _, ko, hist = o.relax(dt_vd / 40, 40)
+    assert kg == ko
+    assert Eg == pytest.approx(hist[-1], rel=1e-6)
+    compare(g, o, 2, 1e-10)
+
+
+def test_fp64_bubble_channel_full_run_matches_oracle():
+    """The 128x16 bubble channel: 20 drag steps, each followed by up to 50
+    relaxation sub-steps (tolerance 1e-6 on max |du_cr|/U), and 2000 standard
+    steps at the relaxation time-step; every field within 1e-10 relative."""
+    c = inputs.channel_bubble_2d()
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"])
+    assert N == 50
+    g, o, kg, ko = run_oscar_pair(c, c.meta["n_drag"], N, dt_vd, dt_vd / N)
+    assert kg == ko
+    worst = compare(g, o, 2, 1e-10)
+    print("oscar worst rel err", max(worst.values()))
+    gs = ox.Oscar(c.params, c.solid, c.alpha0)
+    os_ = oracle.OracleState(c.params, c.solid, c.alpha0)
+    for _ in range(c.meta["n_standard"]):
+        gs.standard_step(dt_vd / N)
+        os_.standard_step(dt_vd / N)
+    worst = compare(gs, os_, 2, 1e-10, skip=("ucrx", "ucry", "phi_cr_x", "phi_cr_y"))
+    print("standard worst rel err", max(worst.values()))
+
+
+def _bubble_velocity(st, is_oracle):
+    a = st.field(oracle.ALPHA if is_oracle else ox.FIELD_ALPHA)
+    u = st.field(oracle.UX if is_oracle else ox.FIELD_U)
+    return (a * u).sum() / a.sum()
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.channel_bubble_2d(),
+                                  lambda: inputs.random_small_case(5, 20, 12, nz=10, dim=3)])
+def test_mixed_precision_within_tolerance(make):
+    c = make()
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta.get("c_cfl", 0.02))
+    g, o, kg, ko = run_oscar_pair(c, 3, min(N, 10), dt_vd, dt_vd / N, precision=inputs.PREC_MIXED, N=min(N, 10))
+    da = np.abs(g.field(ox.FIELD_ALPHA) - o.field(oracle.ALPHA)).max()
+    assert da <= 1e-5
+    vg, vo = _bubble_velocity(g, False), _bubble_velocity(o, True)
+    assert vg == pytest.approx(vo, rel=5e-3)
+
+
+def test_edge_cases():
+    # all-solid grid is rejected; a single fluid column works
+    c = inputs.random_small_case(6, 5, 4)
+    with pytest.raises(ox.OscarError):
+        ox.Oscar(c.params, np.ones_like(c.solid), c.alpha0)
+    p = inputs.default_params(dim=2, nx=1, ny=1, hx=1e-6, hy=1e-6, U_inlet=1e-3, rho1=1.0, rho2=1.0, sigma=0.01)
+    s = np.zeros((1, 1), np.uint8)
+    a = np.full((1, 1), 0.3)
+    g = ox.Oscar(p, s, a)
+    o = oracle.OracleState(p, s, a)
+    for _ in range(3):
+        g.drag_step(1e-4)
+        o.drag_step(1e-4)
+        g.relax(1e-6, 2)
+        o.relax(1e-6, 2)
+    compare(g, o, 2, 1e-10)
+
+
+@pytest.mark.parametrize("which", ["constriction_3d", "micromodel_2d"])
+def test_full_size_invariants(which):
+    """At the bench's full sizes (mixed precision): alpha stays in [0, 1], face
+    fluxes are divergence-free to the solver tolerance, the phase volume
+    changes only by what crosses inlet and outlet, and nothing is non-finite."""
+    c = inputs.constricted_channel_3d() if which == "constriction_3d" else inputs.micromodel_2d()
+    p = c.params
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"])
+    g = ox.Oscar(p, c.solid, c.alpha0)
+    v0 = g.stats()["phase_volume"]
+    g.drag_step(dt_vd)
+    g.relax(dt_vd / N, 3)
+    a = g.field(ox.FIELD_ALPHA)
+    assert np.isfinite(a).all()
+    assert a.min() >= -1e-5 and a.max() <= 1 + 1e-5
+    for base in (ox.FIELD_PHI_VD, ox.FIELD_PHI_CR):
+        phi = [g.field(base + d) for d in range(p["dim"])]
+        if p["dim"] == 2:
+            div = (phi[0][:, 1:] - phi[0][:, :-1]) + (phi[1][1:, :] - phi[1][:-1, :])
+        else:
+            div = ((phi[0][:, :, 1:] - phi[0][:, :, :-1]) + (phi[1][:, 1:, :] - phi[1][:, :-1, :])
+                   + (phi[2][1:, :, :] - phi[2][:-1, :, :]))
+        scale = max(np.abs(x).max() for x in phi)
+        assert np.abs(div[c.solid == 0]).max() <= 1e-5 * scale
+    # volume balance: the drag step moves alpha_inlet * inflow * dt in
+    phix = g.field(ox.FIELD_PHI_VD)
+    v1 = g.stats()["phase_volume"]
+    assert abs(v1 - v0) <= 2.0 * abs(phix[..., 0]).sum() * dt_vd + 1e-6 * v0

@@ -494,21 +494,26 @@ def test_static_drop_mirror_symmetry_in_y():
 # Momentum terms of Eqs. NSE1d / NSEc (explicit part H of PISO)
 # ---------------------------------------------------------------------------
 def test_linear_upwind_convection_exact_for_quadratic():
-    """With mu = 0 and a uniform convecting flux U S, HbyA = v_old - dt U dv/dx;
-    linear upwinding (Section 4) differentiates v = x^2 exactly."""
+    """mu = 0, uniform convecting flux U S, v_old = v: the momentum equation
+    A v - H = rho (phic . grad) v, so HbyA = v - rA rho U dv/dx, and linear
+    upwinding (Section 4; upwind part implicit, correction explicit)
+    differentiates v = x^2 exactly."""
     nx, ny, h = 14, 3, 1e-6
-    p = inputs.default_params(dim=2, nx=nx, ny=ny, hx=h, hy=h, mu1=0.0, mu2=0.0, rho1=2.0, rho2=2.0)
+    rho = 2.0
+    p = inputs.default_params(dim=2, nx=nx, ny=ny, hx=h, hy=h, mu1=0.0, mu2=0.0, rho1=rho, rho2=rho)
     s = np.zeros((ny, nx), np.uint8)
     x = (np.arange(nx) + 0.5) * h
     vx = np.tile((x / h) ** 2, (ny, 1))
     U, dt = 1e-3, 1e-7
     phx = np.full((ny, nx + 1), U * h)
     phy = np.zeros((ny + 1, nx))
-    (hx, hy), rA = oracle.stage_momentum(p, s, [vx, 0 * vx], [0 * vx, 0 * vx], [phx, phy],
+    (hx, hy), rA = oracle.stage_momentum(p, s, [vx, 0 * vx], [vx, 0 * vx], [phx, phy],
                                           np.zeros((ny, nx)), vin_x=0.0, dt=dt)
     dvdx = 2 * x / h / h
     for i in range(2, nx - 2):
-        assert hx[1, i] == pytest.approx(-dt * U * dvdx[i], rel=1e-12)
+        assert hx[1, i] == pytest.approx(vx[1, i] - rA[1, i] * rho * U * dvdx[i], rel=1e-12)
+    # implicit upwind: the inflow flux sits on the diagonal A = rho/dt + rho U S / V
+    assert rA[1, 5] == pytest.approx(1.0 / (rho / dt + rho * U / h), rel=1e-14)
     assert np.abs(hy).max() == 0.0
 
 
@@ -529,3 +534,30 @@ def test_transpose_viscous_term_shear_with_linear_viscosity():
     dmudx = (mu1 - mu2) / (nx * h)
     inner = (slice(1, ny - 1), slice(1, nx - 1))
     np.testing.assert_allclose(hy[inner], rA[inner] * gam * dmudx, rtol=1e-10)
+
+
+def test_normalised_residual_zero_rhs_zero_mean_guess_is_one():
+    """For b = 0 and a zero-mean guess q (so M qbar = 0) the normalised residual
+    sum|Mq| / (sum|Mq - M qbar| + sum|b - M qbar|) equals exactly 1."""
+    rng = np.random.default_rng(9)
+    case = inputs.random_small_case(10, 9, 7)
+    p, s = case.params, case.solid
+    cf = _coeffs(p, s, rng)
+    q = rng.standard_normal(s.shape) * (s == 0)
+    q[s == 0] -= q[s == 0].mean()
+    E = oracle.stage_normalised_residual(p, s, cf, np.zeros_like(q), q)
+    assert E == pytest.approx(1.0, rel=1e-9)
+
+
+def test_smoothing_is_area_weighted_on_anisotropic_cells():
+    """One smoothing pass of alpha = x^2 on cells hx != hy: interior value
+    x^2 + hx^2 S_x / (2 (S_x + S_y)) with S_x = hy, S_y = hx (face-area
+    weighted average of linearly interpolated face values)."""
+    nx, ny, hx, hy = 12, 6, 1.0, 0.25
+    p = inputs.default_params(dim=2, nx=nx, ny=ny, hx=hx, hy=hy, n_smooth=1)
+    s = np.zeros((ny, nx), np.uint8)
+    x = (np.arange(nx) + 0.5) * hx
+    a = np.tile(x ** 2, (ny, 1))
+    als, _, _ = oracle.stage_interface(p, s, a)
+    expect = x ** 2 + hx ** 2 * hy / (2 * (hy + hx))
+    np.testing.assert_allclose(als[2:-2, 1:-1], np.tile(expect[1:-1], (ny - 4, 1)), rtol=1e-13)
