@@ -155,9 +155,9 @@ int oscar_destroy(oscar_handle h);
 const char *oscar_strerror(int code);
 
 /* Kernel-class timing with CUDA events on the handle's stream (measurement
- * support, not part of the method). enable = 1 starts recording every launch
- * of the classes below (events from a fixed pool; records past its capacity
- * are dropped and counted), 0 stops. oscar_profile_read waits for the stream
+ * support, not part of the method). enable = 1 starts recording every eager
+ * launch of the classes below (the step calls run as captured graphs, whose
+ * loop bodies hold no event nodes, so they are not recorded), 0 stops. oscar_profile_read waits for the stream
  * and returns, for class kid, the summed device time [ms] and the number of
  * launches recorded since the last reset; reset = 1 clears all classes. */
 #define OSCAR_KID_RBGS0 0      /* red-black Gauss-Seidel half-sweep, finest level */
@@ -168,6 +168,13 @@ const char *oscar_strerror(int code);
 #define OSCAR_KID_COUNT 5
 int oscar_profile(oscar_handle h, int enable);
 int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset);
+
+/* Launch kernel class kid reps times back to back on the current state of the
+ * instance (outside any graph; the kernels write only scratch buffers, so the
+ * state is unchanged) and return the mean device time per launch [ms], timed
+ * with CUDA events on the handle's stream. The class TRANSPORT counts its
+ * three kernels as one launch. Waits for the stream. */
+int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms);
 
 #ifdef __cplusplus
 }

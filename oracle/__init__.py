@@ -319,3 +319,23 @@ def stage_momentum(p, solid, v, v_old, phic, alpha_new, vin_x=0.0, dt=1e-7):
     lib.or_stage_momentum(C.byref(P), _u8(s), *[_dp(x) for x in vv], *[_dp(x) for x in vo],
                           *[_dp(x) for x in pc], _dp(an), vin_x, dt, *[_dp(x) for x in hb], _dp(rA))
     return hb[: p["dim"]], rA
+
+
+def stage_poisson_banded(p, solid, cf, b):
+    """Exact pressure solve by banded Cholesky (shortest axis numbered fastest)."""
+    lib = _load()
+    if not hasattr(lib, "_band_ready"):
+        dp = C.POINTER(C.c_double)
+        lib.or_stage_poisson_banded.restype = C.c_int
+        lib.or_stage_poisson_banded.argtypes = [C.POINTER(OrParams), C.POINTER(C.c_uint8)] + [dp] * 5
+        lib._band_ready = True
+    P = make_params(p)
+    sh = grid_shape(p)
+    s = np.ascontiguousarray(solid, np.uint8).reshape(sh)
+    c3 = _faces3(p, cf)
+    bb = np.ascontiguousarray(b, np.float64).reshape(sh)
+    q = np.zeros(sh)
+    rc = lib.or_stage_poisson_banded(C.byref(P), _u8(s), *[_dp(x) for x in c3], _dp(bb), _dp(q))
+    if rc != 0:
+        raise RuntimeError(f"banded Cholesky failed ({rc})")
+    return q

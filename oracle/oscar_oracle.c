@@ -39,6 +39,9 @@
 #define OR_CONV_PRES_RESID 0
 #define OR_CONV_DU_MAX 1
 
+/* exact (banded Cholesky) pressure solves up to this many multiply-adds */
+#define OR_BANDED_MAX_WORK 4.0e8
+
 typedef struct {
     int dim, nx, ny, nz;
     double hx, hy, hz;
@@ -524,6 +527,99 @@ int or_poisson_dense(const or_grid *g, double *const cf[3], const double *b, dou
     return 0;
 }
 
+/* Banded Cholesky solve of M q = b over fluid cells: the exact solution of
+ * the pressure equation up to rounding. Cells are numbered with the shortest
+ * axis fastest so the bandwidth is the product of the two shortest extents.
+ * Returns -1 if M is not positive definite, -2 if the band is too wide
+ * (more than max_work multiply-adds). */
+int or_poisson_banded(const or_grid *g, double *const cf[3], const double *b, double *q, double max_work) {
+    int nc = g->ncell;
+    int ax[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)   /* sort axes by extent, shortest first (x wins ties) */
+        for (int j = i + 1; j < 3; ++j)
+            if (g->n[ax[j]] < g->n[ax[i]]) { int t = ax[i]; ax[i] = ax[j]; ax[j] = t; }
+    int *map = malloc(nc * sizeof(int));
+    int m = 0;
+    int ijk[3];
+    for (int s2 = 0; s2 < g->n[ax[2]]; ++s2)
+        for (int s1 = 0; s1 < g->n[ax[1]]; ++s1)
+            for (int s0 = 0; s0 < g->n[ax[0]]; ++s0) {
+                ijk[ax[0]] = s0; ijk[ax[1]] = s1; ijk[ax[2]] = s2;
+                int c = cidx(g, ijk[0], ijk[1], ijk[2]);
+                map[c] = g->solid[c] ? -1 : m++;
+            }
+    /* bandwidth over the couplings of the operator */
+    int bw = 0;
+    for (int c = 0; c < nc; ++c) {
+        if (map[c] < 0) continue;
+        for (int a = 0; a < g->dim; ++a)
+            for (int s = 0; s < 2; ++s) {
+                int f, nb;
+                if (cell_face(g, c, a, s, &f, &nb) == OR_F_INTERIOR) {
+                    int d = map[c] > map[nb] ? map[c] - map[nb] : map[nb] - map[c];
+                    if (d > bw) bw = d;
+                }
+            }
+    }
+    if ((double)m * (bw + 1) * (bw + 1) > max_work) { free(map); return -2; }
+    int W = bw + 1;   /* row r holds A(r, r-d) at L[r*W + d] */
+    double *L = calloc((size_t)m * W, sizeof(double));
+    for (int c = 0; c < nc; ++c) {
+        int r = map[c];
+        if (r < 0) continue;
+        double diag = 0.0;
+        for (int a = 0; a < g->dim; ++a)
+            for (int s = 0; s < 2; ++s) {
+                int f, nb;
+                int t = cell_face(g, c, a, s, &f, &nb);
+                if (t == OR_F_INTERIOR) {
+                    diag += cf[a][f];
+                    int rn = map[nb];
+                    if (rn < r) L[(size_t)r * W + (r - rn)] -= cf[a][f];
+                } else if (t == OR_F_OUTLET) {
+                    diag += cf[a][f];
+                }
+            }
+        L[(size_t)r * W] = diag;
+    }
+    /* in-place band Cholesky: A = L L^T */
+    for (int j = 0; j < m; ++j) {
+        double sum = L[(size_t)j * W];
+        int k0 = j - bw > 0 ? j - bw : 0;
+        for (int k = k0; k < j; ++k) {
+            double ljk = L[(size_t)j * W + (j - k)];
+            sum -= ljk * ljk;
+        }
+        if (sum <= 0.0) { free(map); free(L); return -1; }
+        double ljj = sqrt(sum);
+        L[(size_t)j * W] = ljj;
+        int i1 = j + bw < m - 1 ? j + bw : m - 1;
+        for (int i = j + 1; i <= i1; ++i) {
+            double t = L[(size_t)i * W + (i - j)];
+            int kk0 = i - bw > k0 ? i - bw : k0;
+            for (int k = kk0; k < j; ++k) t -= L[(size_t)i * W + (i - k)] * L[(size_t)j * W + (j - k)];
+            L[(size_t)i * W + (i - j)] = t / ljj;
+        }
+    }
+    double *y = calloc(m, sizeof(double));
+    for (int c = 0; c < nc; ++c) if (map[c] >= 0) y[map[c]] = b[c];
+    for (int i = 0; i < m; ++i) {   /* L y' = y */
+        double t = y[i];
+        int k0 = i - bw > 0 ? i - bw : 0;
+        for (int k = k0; k < i; ++k) t -= L[(size_t)i * W + (i - k)] * y[k];
+        y[i] = t / L[(size_t)i * W];
+    }
+    for (int i = m - 1; i >= 0; --i) {   /* L^T q = y' */
+        double t = y[i];
+        int k1 = i + bw < m - 1 ? i + bw : m - 1;
+        for (int k = i + 1; k <= k1; ++k) t -= L[(size_t)k * W + (k - i)] * y[k];
+        y[i] = t / L[(size_t)i * W];
+    }
+    for (int c = 0; c < nc; ++c) q[c] = map[c] >= 0 ? y[map[c]] : 0.0;
+    free(map); free(L); free(y);
+    return 0;
+}
+
 /* Normalised L1 residual of M q = b: sum|b - Mq| / (sum|Mq - M qbar| + sum|b - M qbar| + 1e-20),
  * qbar the mean of q over fluid cells (Section 3.2, "normalized norm"). */
 double or_normalised_residual(const or_grid *g, double *const cf[3], const double *b, const double *q) {
@@ -721,8 +817,13 @@ static void piso(const or_grid *g, const or_params *P,
             b[c] = -div;
         }
         if (corr == 0) out->E = or_normalised_residual(g, cf, b, q);
-        int it = or_poisson_cg(g, cf, b, q, P->cg_rtol, P->cg_maxit);
-        if (it < 0) { out->cg_fail = 1; it = -it; }
+        /* the pressure equation is solved exactly (banded Cholesky) where the
+         * band is narrow, else by Jacobi-PCG to cg_rtol */
+        int it = 0;
+        if (or_poisson_banded(g, cf, b, q, OR_BANDED_MAX_WORK) != 0) {
+            it = or_poisson_cg(g, cf, b, q, P->cg_rtol, P->cg_maxit);
+            if (it < 0) { out->cg_fail = 1; it = -it; }
+        }
         out->cg_iters += it;
         /* flux correction phi = phi* - c_f (q_H - q_L) */
         for (int a = 0; a < D; ++a) {
@@ -1093,4 +1194,12 @@ void or_stage_momentum(const or_params *P, const uint8_t *solid,
     free(rho_n); free(mu_n);
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) free(G[a][b]);
+}
+
+int or_stage_poisson_banded(const or_params *P, const uint8_t *solid, double *cx, double *cy, double *cz,
+                            const double *b, double *q) {
+    or_grid g;
+    grid_init(&g, P, solid);
+    double *cf[3] = {cx, cy, cz};
+    return or_poisson_banded(&g, cf, b, q, 1e18);
 }

@@ -36,7 +36,7 @@ int sync_bounded(cudaStream_t s, double timeout_sec) {
 
 int prof_begin(Instance &I, int kid) {
     Profiler *P = I.prof;
-    if (!P || !P->enabled) return -1;
+    if (!P || !P->enabled || I.capturing) return -1;   // no event nodes inside captured graphs
     if (P->n >= kProfPool) {
         // drain: wait for the recorded launches and accumulate their times
         if (sync_bounded(I.stream, kSyncTimeoutSec)) { P->dropped++; return -1; }
@@ -165,6 +165,7 @@ static void carve(Instance &I, Carver &C) {
     I.stage_dev = (double *)C.take(I.stage_len * sizeof(double));
     I.partials = (double *)C.take((size_t)kRedSlots * kRedBlocks * sizeof(double));
     I.scal = (double *)C.take(S_COUNT * sizeof(double));
+    I.ctl = (int *)C.take(C_COUNT * sizeof(int));
 }
 
 static int validate(const oscar_params *p) {
@@ -255,7 +256,11 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     }
     Carver wet{(char *)I.arena, 0, false};
     carve(I, wet);
-    if (cudaMallocHost(&I.scal_host, S_COUNT * sizeof(double)) != cudaSuccess ||
+    bool streams_ok = true;
+    for (int q = 0; q < 4; ++q)
+        if (cudaStreamCreateWithFlags(&I.side[q], cudaStreamNonBlocking) != cudaSuccess) streams_ok = false;
+    if (!streams_ok || cudaMallocHost(&I.scal_host, S_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&I.ctl_host, C_COUNT * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&I.stage_host, stage * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(I.arena);
@@ -284,8 +289,13 @@ int oscar_destroy(oscar_handle h) {
     Instance &I = h->I;
     if (I.arena) {
         sync_bounded(I.stream, kSyncTimeoutSec);
+        if (I.prec == OSCAR_FP64) Solver<double>::release_graphs(I);
+        else Solver<float>::release_graphs(I);
         cudaFree(I.arena);
     }
+    for (int q = 0; q < 4; ++q)
+        if (I.side[q]) cudaStreamDestroy(I.side[q]);
+    if (I.ctl_host) cudaFreeHost(I.ctl_host);
     if (I.prof) {
         if (I.prof->created)
             for (int s = 0; s < kProfPool; ++s) { cudaEventDestroy(I.prof->ev0[s]); cudaEventDestroy(I.prof->ev1[s]); }
@@ -377,7 +387,7 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out) {
     out->n_fluid = I.n_fluid;
     out->cell_updates = I.cell_updates;
     out->device_bytes = I.arena_bytes;
-    out->kernel_launches = I.nlaunch;
+    out->kernel_launches = I.nexec;
     return 0;
 }
 
@@ -402,6 +412,13 @@ int oscar_profile(oscar_handle h, int enable) {
     }
     I.prof->enabled = enable ? 1 : 0;
     return 0;
+}
+
+int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms) {
+    if (!h || !avg_ms || reps < 1 || kid < 0 || kid >= OSCAR_KID_COUNT) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    return I.prec == OSCAR_FP64 ? Solver<double>::profile_kernel(I, kid, reps, avg_ms)
+                                : Solver<float>::profile_kernel(I, kid, reps, avg_ms);
 }
 
 int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset) {

@@ -17,7 +17,21 @@ constexpr double kSyncTimeoutSec = 600.0;
 
 // Scalar slots in the device scalar array (double).
 enum Slot {
-    S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_R0, S_TMP, S_COUNT
+    S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_TARGET, S_E, S_DU, S_TEST,
+    S_TMP, S_COUNT
+};
+
+// Integer control words on the device (relaxation and PCG loop state).
+enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COUNT = 8 };
+
+// One captured and instantiated step graph.
+struct GraphSlot {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    double dt;
+    int valid;
+    long long n_pre;    // kernels outside every loop body
+    long long n_body;   // kernels per relaxation sub-step outside the PCG bodies
 };
 
 struct GridH {
@@ -91,8 +105,19 @@ struct Instance {
     int cg_iters_last;
     long long cell_updates;
     int mg_nu, mg_coarse_sweeps;
-    long long nlaunch;     // kernels launched by this instance
+    long long nlaunch;     // kernel launches issued by the host (eager or into a capture)
+    long long nexec;       // kernels executed on the device (graph executions counted by loop trips)
     Profiler *prof;
+    // graphs: 0 drag step, 1 relaxation, 2 standard step
+    GraphSlot gslot[3];
+    cudaStream_t side[4];  // capture streams of nested loop bodies
+    int depth;             // current nesting depth while capturing
+    int capturing;
+    long long n_cg_body;   // kernels per PCG iteration
+    long long cg_bodies_captured;
+    int *ctl;              // device control words
+    int *ctl_host;         // pinned: initial control words (read by the graph) and read-back
+    double last_dt;
 };
 
 int prof_begin(Instance &I, int kid);
@@ -107,6 +132,8 @@ template <typename T> struct Solver {
     static int field_to_device(Instance &I, int which, double *dst, size_t n);
     static int field_from_device(Instance &I, int which, const double *src, size_t n);
     static int phase_volume(Instance &I, double *out);
+    static int profile_kernel(Instance &I, int kid, int reps, double *avg_ms);
+    static void release_graphs(Instance &I);
 };
 
 int sync_bounded(cudaStream_t s, double timeout_sec);

@@ -929,472 +929,4 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> c, 
     diag[cell] = acc;
 }
 
-// ---------------------------------------------------------------------------
-// host orchestration
-// ---------------------------------------------------------------------------
-#define OSCAR_LAUNCH_CHECK()                                        \
-    do {                                                            \
-        cudaError_t e_ = cudaGetLastError();                        \
-        if (e_ != cudaSuccess) {                                    \
-            fprintf(stderr, "oscar: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
-            return OSCAR_E_CUDA;                                    \
-        }                                                           \
-    } while (0)
-
-inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
-
-template <typename T> struct Impl {
-    using M = T;
-    static T *tp(void *p) { return (T *)p; }
-
-    static int final_sum(Instance &I, int slot_part, int slot_out, bool is_max = false) {
-        k_final<<<1, 1024, 0, I.stream>>>(I.partials + slot_part * kRedBlocks, kRedBlocks, I.scal + slot_out,
-                                          is_max ? 1 : 0), ++I.nlaunch;
-        return 0;
-    }
-    static int read_scalars(Instance &I) {
-        if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) !=
-            cudaSuccess)
-            return OSCAR_E_CUDA;
-        return sync_bounded(I.stream, kSyncTimeoutSec);
-    }
-    static C3<T> c3(void *const *p) { C3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (const T *)p[a]; return r; }
-    static P3<T> p3(void *const *p) { P3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (T *)p[a]; return r; }
-
-    // --- transport ---------------------------------------------------------
-    template <int DIM>
-    static int transport_d(Instance &I, void *const *phi, double dt) {
-        GridD g = to_dev(I.g);
-        T rV = (T)(dt / I.g.V);
-        int nb = nblk(g.ncell);
-        int ps = prof_begin(I, OSCAR_KID_TRANSPORT);
-        k_transport_low<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf), (T)I.P.c_alpha,
-                                                         (T)I.P.alpha_inlet, rV, tp(I.aL), tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
-        k_transport_ratio<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp), tp(I.Pm), rV,
-                                                           tp(I.Rp), tp(I.Rm)), ++I.nlaunch;
-        k_transport_update<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
-                                                            (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
-                                                            tp(I.alpha_new)), ++I.nlaunch;
-        prof_end(I, ps);
-        OSCAR_LAUNCH_CHECK();
-        return 0;
-    }
-    static int transport(Instance &I, void *const *phi, double dt) {
-        return I.g.dim == 3 ? transport_d<3>(I, phi, dt) : transport_d<2>(I, phi, dt);
-    }
-
-    // --- interface ---------------------------------------------------------
-    template <int DIM>
-    static int interface_d(Instance &I, void *alpha) {
-        GridD g = to_dev(I.g);
-        int nb = nblk(g.ncell);
-        void *src = alpha;
-        for (int pass = 0; pass < I.P.n_smooth; ++pass) {
-            void *dst = (pass % 2 == 0) ? I.alpha_s : I.alpha_tmp;
-            k_smooth<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(src), tp(dst)), ++I.nlaunch;
-            src = dst;
-        }
-        const T *as = tp(src);
-        T ct = (T)I.cos_theta, dn = (T)I.deltaN;
-        k_normals<DIM, 0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
-        k_normals<DIM, 1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
-        if (DIM == 3)
-            k_normals<DIM, 2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
-        k_curvature<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
-        return 0;
-    }
-    static int interface_(Instance &I, void *alpha) {
-        return I.g.dim == 3 ? interface_d<3>(I, alpha) : interface_d<2>(I, alpha);
-    }
-
-    // --- multigrid -----------------------------------------------------------
-    template <int DIM>
-    static int mg_coeffs_d(Instance &I) {
-        for (int l = 0; l < I.nlev; ++l) {
-            Level &L = I.lev[l];
-            GridD g = to_dev(L.g);
-            if (l > 0) {
-                Level &F = I.lev[l - 1];
-                GridD gf = to_dev(F.g);
-                k_mg_coarse_coeff<0, M><<<nblk(L.g.nf[0]), BS, 0, I.stream>>>(gf, g, L.g.nf[0], F.r[0], F.r[1], F.r[2],
-                                                                          (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
-                k_mg_coarse_coeff<1, M><<<nblk(L.g.nf[1]), BS, 0, I.stream>>>(gf, g, L.g.nf[1], F.r[0], F.r[1], F.r[2],
-                                                                          (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
-                if (DIM == 3)
-                    k_mg_coarse_coeff<2, M><<<nblk(L.g.nf[2]), BS, 0, I.stream>>>(gf, g, L.g.nf[2], F.r[0], F.r[1],
-                                                                              F.r[2], (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
-            }
-            MG3<M> c;
-            for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
-            k_mg_diag<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (M *)L.diag), ++I.nlaunch;
-        }
-        OSCAR_LAUNCH_CHECK();
-        return 0;
-    }
-
-    template <int DIM>
-    static void smooth_level(Instance &I, int l, int colour) {
-        Level &L = I.lev[l];
-        GridD g = to_dev(L.g);
-        MG3<M> c;
-        for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
-        int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
-        k_mg_rbgs<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag, (M *)L.x,
-                                                              (const M *)L.b, colour), ++I.nlaunch;
-        prof_end(I, ps);
-    }
-
-    // z = V-cycle(r)
-    template <int DIM>
-    static int vcycle_d(Instance &I, const double *r, double *z) {
-        int n0 = I.g.ncell;
-        k_convert<double, M><<<nblk(n0), BS, 0, I.stream>>>(n0, r, (M *)I.lev[0].b), ++I.nlaunch;
-        k_fill<M><<<nblk(n0), BS, 0, I.stream>>>(n0, (M *)I.lev[0].x, M(0)), ++I.nlaunch;
-        int nu = I.mg_nu;
-        for (int l = 0; l < I.nlev - 1; ++l) {
-            Level &L = I.lev[l], &C = I.lev[l + 1];
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0); smooth_level<DIM>(I, l, 1); }
-            GridD g = to_dev(L.g), gc = to_dev(C.g);
-            MG3<M> c;
-            for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
-            int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-            k_mg_residual<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag,
-                                                                      (const M *)L.x, (const M *)L.b, (M *)L.res), ++I.nlaunch;
-            prof_end(I, ps);
-            k_mg_restrict<M><<<nblk(gc.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], (const M *)L.res,
-                                                                  (M *)C.b, (M *)C.x), ++I.nlaunch;
-        }
-        int lc = I.nlev - 1;
-        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 0); smooth_level<DIM>(I, lc, 1); }
-        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 1); smooth_level<DIM>(I, lc, 0); }
-        for (int l = I.nlev - 2; l >= 0; --l) {
-            Level &L = I.lev[l], &C = I.lev[l + 1];
-            GridD g = to_dev(L.g), gc = to_dev(C.g);
-            k_mg_prolong<M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
-                                                                (const M *)C.x, (M *)L.x), ++I.nlaunch;
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1); smooth_level<DIM>(I, l, 0); }
-        }
-        k_convert<M, double><<<nblk(n0), BS, 0, I.stream>>>(n0, (const M *)I.lev[0].x, z), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
-        return 0;
-    }
-
-    // PCG for M q = b; returns iterations (>=0) or a negative error code.
-    template <int DIM>
-    static int pcg_d(Instance &I, double *q, const double *b, int *not_conv) {
-        GridD g = to_dev(I.g);
-        C3<T> cf = c3(I.lev[0].c);
-        int n = g.ncell;
-        double *part = I.partials;
-        k_cg_init<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, q, b, I.cg_r, part, part + kRedBlocks), ++I.nlaunch;
-        final_sum(I, 0, S_BB);
-        final_sum(I, 1, S_RR);
-        OSCAR_LAUNCH_CHECK();
-        int rc = read_scalars(I);
-        if (rc) return rc;
-        double bn = sqrt(I.scal_host[S_BB]), rn = sqrt(I.scal_host[S_RR]);
-        if (!isfinite(bn) || !isfinite(rn)) return OSCAR_E_NAN;
-        double target = I.P.cg_rtol * (bn > 0.0 ? bn : rn);
-        if (rn <= target) return 0;
-        vcycle_d<DIM>(I, I.cg_r, I.cg_z);
-        k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
-        int cur = S_RZ0, nxt = S_RZ1;
-        final_sum(I, 0, cur);
-        k_cg_pupdate<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, cur, cur, 1, I.cg_z, I.cg_p), ++I.nlaunch;
-        int it;
-        for (it = 1; it <= I.P.cg_maxit; ++it) {
-            int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-            k_cg_apply_dot<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-            prof_end(I, ps);
-            final_sum(I, 0, S_PAP);
-            k_cg_update<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, cur, q, I.cg_r, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-            final_sum(I, 0, S_RR);
-            OSCAR_LAUNCH_CHECK();
-            rc = read_scalars(I);
-            if (rc) return rc;
-            rn = sqrt(I.scal_host[S_RR]);
-            if (!isfinite(rn)) return OSCAR_E_NAN;
-            if (rn <= target) break;
-            vcycle_d<DIM>(I, I.cg_r, I.cg_z);
-            k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
-            final_sum(I, 0, nxt);
-            k_cg_pupdate<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, nxt, cur, 0, I.cg_z, I.cg_p), ++I.nlaunch;
-            std::swap(cur, nxt);
-        }
-        if (it > I.P.cg_maxit) { *not_conv = 1; it = I.P.cg_maxit; }
-        return it;
-    }
-
-    // --- PISO ----------------------------------------------------------------
-    template <int DIM>
-    static int piso_d(Instance &I, void *const *v, double *q, void *const *phi, bool has_st, double vin0, double dt,
-                      double *E_out, int *its_out, int *not_conv) {
-        GridD g = to_dev(I.g);
-        int nb = nblk(g.ncell);
-        Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
-        const T *al = tp(I.alpha_new);
-        k_rA<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
-        void **cf = I.lev[0].c;
-        T sig = (T)I.P.sigma;
-        int st = has_st ? 1 : 0;
-        k_face_coeffs<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.rA), tp(I.kappa), al, sig,
-                                                                 st, tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
-        k_face_coeffs<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.rA), tp(I.kappa), al, sig,
-                                                                 st, tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
-        if (DIM == 3)
-            k_face_coeffs<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.rA), tp(I.kappa), al,
-                                                                     sig, st, tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
-        int rc = mg_coeffs_d<DIM>(I);
-        if (rc) return rc;
-        *its_out = 0;
-        P3<T> Gp0 = p3(&I.G[0]), Gp1 = p3(&I.G[3]), Gp2 = p3(&I.G[6]);
-        C3<T> Gc0 = c3(&I.G[0]), Gc1 = c3(&I.G[3]), Gc2 = c3(&I.G[6]);
-        for (int corr = 0; corr < I.P.n_piso; ++corr) {
-            k_vel_grad<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
-            int ps = prof_begin(I, OSCAR_KID_MOMENTUM);
-            k_momentum_H<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), c3(I.vold), c3(I.phic), al, tp(I.rA), fl,
-                                                          (T)vin0, (T)dt, Gc0, Gc1, Gc2, p3(I.hbya)), ++I.nlaunch;
-            prof_end(I, ps);
-            k_phistar<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.hbya[0]), tp(I.rA),
-                                                                 tp(I.fst[0]), (T)vin0, tp(I.phis[0])), ++I.nlaunch;
-            k_phistar<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.hbya[1]), tp(I.rA),
-                                                                 tp(I.fst[1]), T(0), tp(I.phis[1])), ++I.nlaunch;
-            if (DIM == 3)
-                k_phistar<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.hbya[2]), tp(I.rA),
-                                                                     tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
-            k_rhs<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
-            OSCAR_LAUNCH_CHECK();
-            if (corr == 0) {
-                k_sum_field<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, I.partials), ++I.nlaunch;
-                final_sum(I, 0, S_QSUM);
-                k_normres<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
-                                                                   1.0 / (double)I.n_fluid, I.partials,
-                                                                   I.partials + kRedBlocks), ++I.nlaunch;
-                final_sum(I, 0, S_RES);
-                final_sum(I, 1, S_NRM);
-                OSCAR_LAUNCH_CHECK();
-                rc = read_scalars(I);
-                if (rc) return rc;
-                *E_out = I.scal_host[S_RES] / (I.scal_host[S_NRM] + 1e-20);
-            }
-            int it = pcg_d<DIM>(I, q, I.cg_b, not_conv);
-            if (it < 0) return it;
-            *its_out += it;
-            k_flux_correct<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.phis[0]), tp(cf[0]),
-                                                                      q, tp(phi[0])), ++I.nlaunch;
-            k_flux_correct<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.phis[1]), tp(cf[1]),
-                                                                      q, tp(phi[1])), ++I.nlaunch;
-            if (DIM == 3)
-                k_flux_correct<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.phis[2]),
-                                                                          tp(cf[2]), q, tp(phi[2])), ++I.nlaunch;
-            k_vel_correct<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q, p3(v)), ++I.nlaunch;
-            OSCAR_LAUNCH_CHECK();
-        }
-        return 0;
-    }
-    static int piso(Instance &I, void *const *v, double *q, void *const *phi, bool has_st, double vin0, double dt,
-                    double *E, int *its, int *not_conv) {
-        return I.g.dim == 3 ? piso_d<3>(I, v, q, phi, has_st, vin0, dt, E, its, not_conv)
-                            : piso_d<2>(I, v, q, phi, has_st, vin0, dt, E, its, not_conv);
-    }
-
-    static int copy_fields(Instance &I, void *const *dst, void *const *src, int nfield_is_face) {
-        for (int a = 0; a < I.g.dim; ++a) {
-            size_t n = nfield_is_face ? I.g.nf[a] : I.g.ncell;
-            if (cudaMemcpyAsync(dst[a], src[a], n * sizeof(T), cudaMemcpyDeviceToDevice, I.stream) != cudaSuccess)
-                return OSCAR_E_CUDA;
-        }
-        return 0;
-    }
-    static int sum_faces(Instance &I, void *const *a, void *const *b, void *const *out) {
-        for (int d = 0; d < I.g.dim; ++d)
-            k_sum2<T><<<nblk(I.g.nf[d]), BS, 0, I.stream>>>(I.g.nf[d], tp(a[d]), tp(b[d]), tp(out[d])), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
-        return 0;
-    }
-    static void swap_alpha(Instance &I) { std::swap(I.alpha, I.alpha_new); }
-};
-
-template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev, const double *alpha0_dev) {
-    GridD g = to_dev(I.g);
-    int nb = nblk(g.ncell);
-    if (I.g.dim == 3) k_build_info<3><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    else k_build_info<2><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    k_load_alpha<T><<<nb, BS, 0, I.stream>>>(g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
-    for (int l = 1; l < I.nlev; ++l) {
-        Level &F = I.lev[l - 1], &L = I.lev[l];
-        k_mg_fluid_coarsen<<<nblk(L.g.ncell), BS, 0, I.stream>>>(to_dev(F.g), to_dev(L.g), F.r[0], F.r[1], F.r[2],
-                                                                 F.fluid, L.fluid), ++I.nlaunch;
-    }
-    OSCAR_LAUNCH_CHECK();
-    return Impl<T>::interface_(I, I.alpha);
-}
-
-// Section 3.1: viscous-drag step
-template <typename T> int Solver<T>::drag_step(Instance &I, double dt) {
-    using X = Impl<T>;
-    int rc = X::transport(I, I.phi_vd, dt);
-    if (rc) return rc;
-    if ((rc = X::sum_faces(I, I.phi_vd, I.phi_cr, I.phic))) return rc;
-    if ((rc = X::copy_fields(I, I.vold, I.u_vd, 0))) return rc;
-    double E = 0.0;
-    int its = 0, nc = 0;
-    rc = X::piso(I, I.u_vd, I.p_vd, I.phi_vd, false, I.P.U_inlet, dt, &E, &its, &nc);
-    if (rc) return rc;
-    X::swap_alpha(I);
-    if ((rc = X::interface_(I, I.alpha))) return rc;
-    I.cg_iters_last = its;
-    I.cg_iters_total += its;
-    I.cell_updates += I.n_fluid;
-    return nc ? OSCAR_E_NOT_CONVERGED : 0;
-}
-
-// Section 3.2: capillary-relaxation sub-steps with the early exit and the
-// reconstruction u = u_vd + (1/N) sum_k u_cr^{n,k}
-template <typename T> int Solver<T>::relax(Instance &I, double dt, int N, int *kf_out, double *test_out) {
-    using X = Impl<T>;
-    int rc;
-    for (int a = 0; a < I.g.dim; ++a)
-        if (cudaMemsetAsync(I.u_sum[a], 0, I.g.ncell * sizeof(double), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
-    int kf = 0, nc_any = 0;
-    double test = 0.0;
-    for (int k = 0; k < N; ++k) {
-        if ((rc = X::transport(I, I.phi_cr, dt))) return rc;
-        if ((rc = X::interface_(I, I.alpha_new))) return rc;
-        if ((rc = X::sum_faces(I, I.phi_vd, I.phi_cr, I.phic))) return rc;
-        if ((rc = X::copy_fields(I, I.vold, I.u_cr, 0))) return rc;
-        double E = 0.0;
-        int its = 0, nc = 0;
-        rc = X::piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt, &E, &its, &nc);
-        if (rc) return rc;
-        nc_any |= nc;
-        X::swap_alpha(I);
-        P3<double> us;
-        for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
-        if (I.g.dim == 3)
-            k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, X::c3(I.u_cr), X::c3(I.vold), us,
-                                                                 I.partials), ++I.nlaunch;
-        else
-            k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, X::c3(I.u_cr), X::c3(I.vold), us,
-                                                                 I.partials), ++I.nlaunch;
-        X::final_sum(I, 0, S_DUMAX, true);
-        OSCAR_LAUNCH_CHECK();
-        if ((rc = X::read_scalars(I))) return rc;
-        double dU = I.scal_host[S_DUMAX] / I.P.U_inlet;
-        I.last_E = E;
-        I.last_dU = dU;
-        I.cg_iters_last = its;
-        I.cg_iters_total += its;
-        I.cell_updates += I.n_fluid;
-        kf = k + 1;
-        test = (I.P.conv_mode == OSCAR_CONV_DU_MAX) ? dU : E;
-        if (!isfinite(test)) return OSCAR_E_NAN;
-        if (test < I.P.conv_tol) break;
-    }
-    I.last_kf = kf;
-    I.last_N = N;
-    if (kf_out) *kf_out = kf;
-    if (test_out) *test_out = test;
-    return nc_any ? OSCAR_E_NOT_CONVERGED : 0;
-}
-
-// Section 2.2: standard time-stepping
-template <typename T> int Solver<T>::standard_step(Instance &I, double dt) {
-    using X = Impl<T>;
-    int rc = X::transport(I, I.phi_vd, dt);
-    if (rc) return rc;
-    if ((rc = X::interface_(I, I.alpha_new))) return rc;
-    if ((rc = X::copy_fields(I, I.phic, I.phi_vd, 1))) return rc;
-    if ((rc = X::copy_fields(I, I.vold, I.u_vd, 0))) return rc;
-    double E = 0.0;
-    int its = 0, nc = 0;
-    rc = X::piso(I, I.u_vd, I.p_vd, I.phi_vd, true, I.P.U_inlet, dt, &E, &its, &nc);
-    if (rc) return rc;
-    X::swap_alpha(I);
-    for (int a = 0; a < I.g.dim; ++a)
-        if (cudaMemsetAsync(I.u_sum[a], 0, I.g.ncell * sizeof(double), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
-    I.last_E = E;
-    I.last_N = 1;
-    I.cg_iters_last = its;
-    I.cg_iters_total += its;
-    I.cell_updates += I.n_fluid;
-    return nc ? OSCAR_E_NOT_CONVERGED : 0;
-}
-
-template <typename T>
-__global__ void k_report_u(int n, const T *__restrict__ uvd, const double *__restrict__ usum, double invN,
-                           double *__restrict__ out) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) out[c] = (double)uvd[c] + usum[c] * invN;
-}
-static __global__ void k_add_pd(int n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) out[c] = a[c] + b[c];
-}
-
-template <typename T> int Solver<T>::field_to_device(Instance &I, int which, double *dst, size_t n) {
-    int nc = I.g.ncell;
-    cudaStream_t s = I.stream;
-    auto cvt = [&](const void *src, size_t len) { k_convert<T, double><<<nblk(len), BS, 0, s>>>((int)len, (const T *)src, dst), ++I.nlaunch; };
-    if (which == OSCAR_FIELD_ALPHA) cvt(I.alpha, nc);
-    else if (which == OSCAR_FIELD_P) k_add_pd<<<nblk(nc), BS, 0, s>>>(nc, I.p_vd, I.p_cr, dst), ++I.nlaunch;
-    else if (which >= 2 && which <= 4) {
-        int a = which - 2;
-        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
-        else k_report_u<T><<<nblk(nc), BS, 0, s>>>(nc, (const T *)I.u_vd[a], I.u_sum[a], 1.0 / (double)I.last_N, dst), ++I.nlaunch;
-    } else if (which >= 5 && which <= 10) {
-        int a = (which - 5) % 3;
-        void *const *src = which < 8 ? I.u_vd : I.u_cr;
-        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
-        else cvt(src[a], nc);
-    } else if (which == OSCAR_FIELD_P_VD) cudaMemcpyAsync(dst, I.p_vd, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    else if (which == OSCAR_FIELD_P_CR) cudaMemcpyAsync(dst, I.p_cr, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    else if (which == OSCAR_FIELD_KAPPA) cvt(I.kappa, nc);
-    else if (which >= 14 && which <= 22) {
-        int a = (which - 14) % 3;
-        void *const *src = which < 17 ? I.phi_vd : (which < 20 ? I.phi_cr : I.nf);
-        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
-        else cvt(src[a], I.g.nf[a]);
-    } else return OSCAR_E_INVALID_ARG;
-    OSCAR_LAUNCH_CHECK();
-    return 0;
-}
-
-template <typename T> int Solver<T>::field_from_device(Instance &I, int which, const double *src, size_t n) {
-    int nc = I.g.ncell;
-    cudaStream_t s = I.stream;
-    auto cvt = [&](void *dst, size_t len) { k_convert<double, T><<<nblk(len), BS, 0, s>>>((int)len, src, (T *)dst), ++I.nlaunch; };
-    if (which == OSCAR_FIELD_ALPHA) {
-        k_load_alpha<T><<<nblk(nc), BS, 0, s>>>(nc, I.info, src, (T *)I.alpha), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
-        return Impl<T>::interface_(I, I.alpha);
-    } else if (which >= 5 && which <= 10) {
-        int a = (which - 5) % 3;
-        if (a >= I.g.dim) return OSCAR_E_INVALID_ARG;
-        cvt(which < 8 ? I.u_vd[a] : I.u_cr[a], nc);
-    } else if (which == OSCAR_FIELD_P_VD || which == OSCAR_FIELD_P) {
-        cudaMemcpyAsync(I.p_vd, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    } else if (which == OSCAR_FIELD_P_CR) {
-        cudaMemcpyAsync(I.p_cr, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    } else if (which >= 14 && which <= 19) {
-        int a = (which - 14) % 3;
-        if (a >= I.g.dim) return OSCAR_E_INVALID_ARG;
-        cvt(which < 17 ? I.phi_vd[a] : I.phi_cr[a], I.g.nf[a]);
-    } else return OSCAR_E_INVALID_ARG;
-    OSCAR_LAUNCH_CHECK();
-    return 0;
-}
-
-template <typename T> int Solver<T>::phase_volume(Instance &I, double *out) {
-    k_sum_field<T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const T *)I.alpha, I.g.V, I.partials), ++I.nlaunch;
-    Impl<T>::final_sum(I, 0, S_VOL);
-    OSCAR_LAUNCH_CHECK();
-    int rc = Impl<T>::read_scalars(I);
-    if (rc) return rc;
-    *out = I.scal_host[S_VOL];
-    return 0;
-}
-
 }  // namespace oscar

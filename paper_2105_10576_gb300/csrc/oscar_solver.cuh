@@ -1,0 +1,722 @@
+// Orchestration of the OSCAR steps (Maes & Menke, arXiv 2105.10576,
+// Sections 2.2, 3.1, 3.2) as CUDA graphs.
+//
+// Each API call (drag step, relaxation, standard step) launches one
+// instantiated graph and synchronises once. Inside the graph the PCG loop of
+// every pressure solve is a conditional WHILE node whose body ends in a
+// one-thread control kernel (convergence test on the FP64 residual norm), and
+// the relaxation loop is an outer WHILE node whose control kernel applies the
+// paper's early exit (E_k < tol or k = N) on the device. Graphs are captured
+// from the same launch sequence an eager run would issue and are rebuilt
+// when the time step changes.
+#pragma once
+#include <string.h>
+
+#include "oscar_kernels.cuh"
+
+namespace oscar {
+
+#define OSCAR_LAUNCH_CHECK()                                                                              \
+    do {                                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                                              \
+        if (e_ != cudaSuccess) {                                                                          \
+            fprintf(stderr, "oscar: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return OSCAR_E_CUDA;                                                                          \
+        }                                                                                                 \
+    } while (0)
+
+inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
+
+// ---------------------------------------------------------------------------
+// control kernels (one thread)
+// ---------------------------------------------------------------------------
+static __global__ void k_cg_init_check(double *scal, int *ctl, double rtol, cudaGraphConditionalHandle h) {
+    double bb = scal[S_BB], rr = scal[S_RR];
+    double bn = sqrt(bb), rn = sqrt(rr);
+    double target = rtol * (bn > 0.0 ? bn : rn);
+    scal[S_TARGET] = target;
+    scal[S_RZ0] = 0.0;
+    ctl[C_IT] = 0;
+    bool bad = !(isfinite(bn) && isfinite(rn));
+    if (bad) ctl[C_NAN] = 1;
+    cudaGraphSetConditional(h, (!bad && rn > target) ? 1u : 0u);
+}
+
+static __global__ void k_cg_check(double *scal, int *ctl, int maxit, cudaGraphConditionalHandle h) {
+    int it = ++ctl[C_IT];
+    ctl[C_ITSUM] += 1;
+    double rn = sqrt(scal[S_RR]);
+    scal[S_RZ0] = scal[S_RZ1];
+    bool bad = !isfinite(rn);
+    if (bad) ctl[C_NAN] = 1;
+    bool more = !bad && rn > scal[S_TARGET];
+    if (more && it >= maxit) { ctl[C_NOTCONV] = 1; more = false; }
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// p = z + beta p, beta = rz_new / rz_old (0 on the first iteration)
+static __global__ void k_cg_pupdate2(int n, const double *__restrict__ scal, const double *__restrict__ z,
+                                     double *__restrict__ p) {
+    double ro = scal[S_RZ0];
+    double be = ro != 0.0 ? scal[S_RZ1] / ro : 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
+}
+
+static __global__ void k_set_E(double *scal) { scal[S_E] = scal[S_RES] / (scal[S_NRM] + 1e-20); }
+
+static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, ctl[C_N] > 0 ? 1u : 0u);
+}
+
+// Section 3.2 early exit: stop after sub-step k if k = N or the test value
+// (E_k, or max |du_cr| / U) is below the tolerance.
+static __global__ void k_relax_control(double *scal, int *ctl, int mode, double tol, double invU,
+                                       cudaGraphConditionalHandle h) {
+    int k = ++ctl[C_K];
+    double E = scal[S_E];
+    double dU = scal[S_DUMAX] * invU;
+    double test = mode == OSCAR_CONV_DU_MAX ? dU : E;
+    scal[S_DU] = dU;
+    scal[S_TEST] = test;
+    bool bad = !isfinite(test) || ctl[C_NAN];
+    if (bad) ctl[C_NAN] = 1;
+    bool more = !bad && k < ctl[C_N] && !(test < tol);
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// capture helpers
+// ---------------------------------------------------------------------------
+inline int cond_handle(Instance &I, cudaGraphConditionalHandle *h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    if (cudaStreamGetCaptureInfo(I.stream, &st, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+        return OSCAR_E_CUDA;
+    if (cudaGraphConditionalHandleCreate(h, g, 0, 0) != cudaSuccess) return OSCAR_E_CUDA;
+    return 0;
+}
+
+// Append a WHILE node at the capture point of I.stream and redirect I.stream
+// to capture its body.
+inline int begin_while(Instance &I, cudaGraphConditionalHandle h, cudaStream_t *saved) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(I.stream, &st, nullptr, &g, &deps, &ed, &nd) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+        return OSCAR_E_CUDA;
+    // cudaGraphNodeParams has no default constructor in C++: zero-initialised storage
+    alignas(cudaGraphNodeParams) unsigned char buf[sizeof(cudaGraphNodeParams)];
+    memset(buf, 0, sizeof(buf));
+    cudaGraphNodeParams &np = *reinterpret_cast<cudaGraphNodeParams *>(buf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, g, deps, ed, nd, &np) != cudaSuccess) return OSCAR_E_CUDA;
+    if (cudaStreamUpdateCaptureDependencies(I.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+        cudaSuccess)
+        return OSCAR_E_CUDA;
+    if (I.depth + 1 >= 4) return OSCAR_E_CUDA;
+    cudaStream_t side = I.side[++I.depth];
+    if (cudaStreamBeginCaptureToGraph(side, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess)
+        return OSCAR_E_CUDA;
+    *saved = I.stream;
+    I.stream = side;
+    return 0;
+}
+
+inline int end_while(Instance &I, cudaStream_t saved) {
+    cudaGraph_t body;
+    cudaError_t e = cudaStreamEndCapture(I.stream, &body);
+    I.stream = saved;
+    --I.depth;
+    return e == cudaSuccess ? 0 : OSCAR_E_CUDA;
+}
+
+#define OSCAR_TRY(x)              \
+    do {                          \
+        int rc_ = (x);            \
+        if (rc_) return rc_;      \
+    } while (0)
+
+template <typename T> struct Impl {
+    using M = T;
+    static T *tp(void *p) { return (T *)p; }
+    static C3<T> c3(void *const *p) { C3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (const T *)p[a]; return r; }
+    static P3<T> p3(void *const *p) { P3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (T *)p[a]; return r; }
+
+    static void final_sum(Instance &I, int slot_part, int slot_out, bool is_max = false) {
+        k_final<<<1, 1024, 0, I.stream>>>(I.partials + slot_part * kRedBlocks, kRedBlocks, I.scal + slot_out,
+                                          is_max ? 1 : 0), ++I.nlaunch;
+    }
+
+    // --- transport (Eq. alphaExp) ------------------------------------------
+    template <int DIM>
+    static int transport_d(Instance &I, void *const *phi, double dt) {
+        GridD g = to_dev(I.g);
+        T rV = (T)(dt / I.g.V);
+        int nb = nblk(g.ncell);
+        int ps = prof_begin(I, OSCAR_KID_TRANSPORT);
+        k_transport_low<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf), (T)I.P.c_alpha,
+                                                         (T)I.P.alpha_inlet, rV, tp(I.aL), tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
+        k_transport_ratio<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp), tp(I.Pm), rV,
+                                                           tp(I.Rp), tp(I.Rm)), ++I.nlaunch;
+        k_transport_update<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
+                                                            (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
+                                                            tp(I.alpha_new)), ++I.nlaunch;
+        prof_end(I, ps);
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+    static int transport(Instance &I, void *const *phi, double dt) {
+        return I.g.dim == 3 ? transport_d<3>(I, phi, dt) : transport_d<2>(I, phi, dt);
+    }
+
+    // --- interface (Section 2.1) -------------------------------------------
+    template <int DIM>
+    static int interface_d(Instance &I, void *alpha) {
+        GridD g = to_dev(I.g);
+        int nb = nblk(g.ncell);
+        void *src = alpha;
+        for (int pass = 0; pass < I.P.n_smooth; ++pass) {
+            void *dst = (pass % 2 == 0) ? I.alpha_s : I.alpha_tmp;
+            k_smooth<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(src), tp(dst)), ++I.nlaunch;
+            src = dst;
+        }
+        const T *as = tp(src);
+        T ct = (T)I.cos_theta, dn = (T)I.deltaN;
+        k_normals<DIM, 0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
+        k_normals<DIM, 1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
+        if (DIM == 3)
+            k_normals<DIM, 2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
+        k_curvature<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+    static int interface_(Instance &I, void *alpha) {
+        return I.g.dim == 3 ? interface_d<3>(I, alpha) : interface_d<2>(I, alpha);
+    }
+
+    // --- multigrid -----------------------------------------------------------
+    template <int DIM>
+    static int mg_coeffs_d(Instance &I) {
+        for (int l = 0; l < I.nlev; ++l) {
+            Level &L = I.lev[l];
+            GridD g = to_dev(L.g);
+            if (l > 0) {
+                Level &F = I.lev[l - 1];
+                GridD gf = to_dev(F.g);
+                k_mg_coarse_coeff<0, M><<<nblk(L.g.nf[0]), BS, 0, I.stream>>>(gf, g, L.g.nf[0], F.r[0], F.r[1], F.r[2],
+                                                                          (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
+                k_mg_coarse_coeff<1, M><<<nblk(L.g.nf[1]), BS, 0, I.stream>>>(gf, g, L.g.nf[1], F.r[0], F.r[1], F.r[2],
+                                                                          (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
+                if (DIM == 3)
+                    k_mg_coarse_coeff<2, M><<<nblk(L.g.nf[2]), BS, 0, I.stream>>>(gf, g, L.g.nf[2], F.r[0], F.r[1],
+                                                                              F.r[2], (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
+            }
+            MG3<M> c;
+            for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
+            k_mg_diag<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (M *)L.diag), ++I.nlaunch;
+        }
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+
+    template <int DIM>
+    static void smooth_level(Instance &I, int l, int colour) {
+        Level &L = I.lev[l];
+        GridD g = to_dev(L.g);
+        MG3<M> c;
+        for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
+        int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
+        k_mg_rbgs<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag, (M *)L.x,
+                                                              (const M *)L.b, colour), ++I.nlaunch;
+        prof_end(I, ps);
+    }
+
+    template <int DIM>
+    static void residual_level(Instance &I, int l) {
+        Level &L = I.lev[l];
+        GridD g = to_dev(L.g);
+        MG3<M> c;
+        for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
+        int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
+        k_mg_residual<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag, (const M *)L.x,
+                                                                  (const M *)L.b, (M *)L.res), ++I.nlaunch;
+        prof_end(I, ps);
+    }
+
+    // z = V-cycle(r): symmetric (pre-smoothing red-black, post-smoothing
+    // black-red), so it is a valid preconditioner for CG
+    template <int DIM>
+    static int vcycle_d(Instance &I, const double *r, double *z) {
+        int n0 = I.g.ncell;
+        k_convert<double, M><<<nblk(n0), BS, 0, I.stream>>>(n0, r, (M *)I.lev[0].b), ++I.nlaunch;
+        k_fill<M><<<nblk(n0), BS, 0, I.stream>>>(n0, (M *)I.lev[0].x, M(0)), ++I.nlaunch;
+        int nu = I.mg_nu;
+        for (int l = 0; l < I.nlev - 1; ++l) {
+            Level &L = I.lev[l], &C = I.lev[l + 1];
+            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0); smooth_level<DIM>(I, l, 1); }
+            residual_level<DIM>(I, l);
+            GridD g = to_dev(L.g), gc = to_dev(C.g);
+            k_mg_restrict<M><<<nblk(gc.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], (const M *)L.res,
+                                                                  (M *)C.b, (M *)C.x), ++I.nlaunch;
+        }
+        int lc = I.nlev - 1;
+        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 0); smooth_level<DIM>(I, lc, 1); }
+        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 1); smooth_level<DIM>(I, lc, 0); }
+        for (int l = I.nlev - 2; l >= 0; --l) {
+            Level &L = I.lev[l], &C = I.lev[l + 1];
+            GridD g = to_dev(L.g), gc = to_dev(C.g);
+            k_mg_prolong<M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
+                                                                (const M *)C.x, (M *)L.x), ++I.nlaunch;
+            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1); smooth_level<DIM>(I, l, 0); }
+        }
+        k_convert<M, double><<<nblk(n0), BS, 0, I.stream>>>(n0, (const M *)I.lev[0].x, z), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+
+    // PCG for M q = b (FP64 vectors), captured as init + conditional WHILE loop.
+    template <int DIM>
+    static int pcg_d(Instance &I, double *q, const double *b) {
+        GridD g = to_dev(I.g);
+        C3<T> cf = c3(I.lev[0].c);
+        int n = g.ncell;
+        double *part = I.partials;
+        k_cg_init<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, q, b, I.cg_r, part, part + kRedBlocks), ++I.nlaunch;
+        final_sum(I, 0, S_BB);
+        final_sum(I, 1, S_RR);
+        if (cudaMemsetAsync(I.cg_p, 0, (size_t)n * sizeof(double), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
+        cudaGraphConditionalHandle h;
+        OSCAR_TRY(cond_handle(I, &h));
+        k_cg_init_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, h), ++I.nlaunch;
+        cudaStream_t saved;
+        OSCAR_TRY(begin_while(I, h, &saved));
+        long long n0 = I.nlaunch;
+        vcycle_d<DIM>(I, I.cg_r, I.cg_z);
+        k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
+        final_sum(I, 0, S_RZ1);
+        k_cg_pupdate2<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, I.cg_z, I.cg_p), ++I.nlaunch;
+        int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
+        k_cg_apply_dot<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
+        prof_end(I, ps);
+        final_sum(I, 0, S_PAP);
+        k_cg_update<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, q, I.cg_r, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
+        final_sum(I, 0, S_RR);
+        k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, h), ++I.nlaunch;
+        I.n_cg_body = I.nlaunch - n0;
+        I.cg_bodies_captured += 1;
+        OSCAR_LAUNCH_CHECK();
+        return end_while(I, saved);
+    }
+
+    // --- PISO (Section 2.2) --------------------------------------------------
+    template <int DIM>
+    static int piso_d(Instance &I, void *const *v, double *q, void *const *phi, bool has_st, double vin0, double dt) {
+        GridD g = to_dev(I.g);
+        int nb = nblk(g.ncell);
+        Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
+        const T *al = tp(I.alpha_new);
+        k_rA<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
+        void **cf = I.lev[0].c;
+        T sig = (T)I.P.sigma;
+        int st = has_st ? 1 : 0;
+        k_face_coeffs<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.rA), tp(I.kappa), al, sig,
+                                                                 st, tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
+        k_face_coeffs<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.rA), tp(I.kappa), al, sig,
+                                                                 st, tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
+        if (DIM == 3)
+            k_face_coeffs<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.rA), tp(I.kappa), al,
+                                                                     sig, st, tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        OSCAR_TRY(mg_coeffs_d<DIM>(I));
+        P3<T> Gp0 = p3(&I.G[0]), Gp1 = p3(&I.G[3]), Gp2 = p3(&I.G[6]);
+        C3<T> Gc0 = c3(&I.G[0]), Gc1 = c3(&I.G[3]), Gc2 = c3(&I.G[6]);
+        for (int corr = 0; corr < I.P.n_piso; ++corr) {
+            k_vel_grad<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
+            int ps = prof_begin(I, OSCAR_KID_MOMENTUM);
+            k_momentum_H<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), c3(I.vold), c3(I.phic), al, tp(I.rA), fl,
+                                                          (T)vin0, (T)dt, Gc0, Gc1, Gc2, p3(I.hbya)), ++I.nlaunch;
+            prof_end(I, ps);
+            k_phistar<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.hbya[0]), tp(I.rA),
+                                                                 tp(I.fst[0]), (T)vin0, tp(I.phis[0])), ++I.nlaunch;
+            k_phistar<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.hbya[1]), tp(I.rA),
+                                                                 tp(I.fst[1]), T(0), tp(I.phis[1])), ++I.nlaunch;
+            if (DIM == 3)
+                k_phistar<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.hbya[2]), tp(I.rA),
+                                                                     tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
+            k_rhs<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
+            if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
+                k_sum_field<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, I.partials), ++I.nlaunch;
+                final_sum(I, 0, S_QSUM);
+                k_normres<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
+                                                                   1.0 / (double)I.n_fluid, I.partials,
+                                                                   I.partials + kRedBlocks), ++I.nlaunch;
+                final_sum(I, 0, S_RES);
+                final_sum(I, 1, S_NRM);
+                k_set_E<<<1, 1, 0, I.stream>>>(I.scal), ++I.nlaunch;
+            }
+            OSCAR_LAUNCH_CHECK();
+            OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
+            k_flux_correct<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.phis[0]), tp(cf[0]),
+                                                                      q, tp(phi[0])), ++I.nlaunch;
+            k_flux_correct<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.phis[1]), tp(cf[1]),
+                                                                      q, tp(phi[1])), ++I.nlaunch;
+            if (DIM == 3)
+                k_flux_correct<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.phis[2]),
+                                                                          tp(cf[2]), q, tp(phi[2])), ++I.nlaunch;
+            k_vel_correct<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q, p3(v)), ++I.nlaunch;
+            OSCAR_LAUNCH_CHECK();
+        }
+        return 0;
+    }
+    static int piso(Instance &I, void *const *v, double *q, void *const *phi, bool has_st, double vin0, double dt) {
+        return I.g.dim == 3 ? piso_d<3>(I, v, q, phi, has_st, vin0, dt) : piso_d<2>(I, v, q, phi, has_st, vin0, dt);
+    }
+
+    static int copy_fields(Instance &I, void *const *dst, void *const *src, int is_face) {
+        for (int a = 0; a < I.g.dim; ++a) {
+            size_t n = is_face ? I.g.nf[a] : I.g.ncell;
+            if (cudaMemcpyAsync(dst[a], src[a], n * sizeof(T), cudaMemcpyDeviceToDevice, I.stream) != cudaSuccess)
+                return OSCAR_E_CUDA;
+        }
+        return 0;
+    }
+    static int sum_faces(Instance &I, void *const *a, void *const *b, void *const *out) {
+        for (int d = 0; d < I.g.dim; ++d)
+            k_sum2<T><<<nblk(I.g.nf[d]), BS, 0, I.stream>>>(I.g.nf[d], tp(a[d]), tp(b[d]), tp(out[d])), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+    static int commit_alpha(Instance &I) {
+        return cudaMemcpyAsync(I.alpha, I.alpha_new, (size_t)I.g.ncell * sizeof(T), cudaMemcpyDeviceToDevice,
+                               I.stream) == cudaSuccess ? 0 : OSCAR_E_CUDA;
+    }
+    static int load_ctl(Instance &I) {
+        return cudaMemcpyAsync(I.ctl, I.ctl_host, C_COUNT * sizeof(int), cudaMemcpyHostToDevice, I.stream) ==
+                       cudaSuccess ? 0 : OSCAR_E_CUDA;
+    }
+
+    // --- graph bodies -------------------------------------------------------
+    // Section 3.1: viscous-drag step
+    static int body_drag(Instance &I, double dt) {
+        OSCAR_TRY(load_ctl(I));
+        OSCAR_TRY(transport(I, I.phi_vd, dt));
+        OSCAR_TRY(sum_faces(I, I.phi_vd, I.phi_cr, I.phic));
+        OSCAR_TRY(copy_fields(I, I.vold, I.u_vd, 0));
+        OSCAR_TRY(piso(I, I.u_vd, I.p_vd, I.phi_vd, false, I.P.U_inlet, dt));
+        OSCAR_TRY(commit_alpha(I));
+        return interface_(I, I.alpha);
+    }
+    // Section 2.2: standard time-stepping
+    static int body_standard(Instance &I, double dt) {
+        OSCAR_TRY(load_ctl(I));
+        OSCAR_TRY(transport(I, I.phi_vd, dt));
+        OSCAR_TRY(interface_(I, I.alpha_new));
+        OSCAR_TRY(copy_fields(I, I.phic, I.phi_vd, 1));
+        OSCAR_TRY(copy_fields(I, I.vold, I.u_vd, 0));
+        OSCAR_TRY(piso(I, I.u_vd, I.p_vd, I.phi_vd, true, I.P.U_inlet, dt));
+        OSCAR_TRY(commit_alpha(I));
+        for (int a = 0; a < I.g.dim; ++a)
+            if (cudaMemsetAsync(I.u_sum[a], 0, I.g.ncell * sizeof(double), I.stream) != cudaSuccess)
+                return OSCAR_E_CUDA;
+        return 0;
+    }
+    // Section 3.2: relaxation loop as a WHILE node with the early exit on device
+    static int body_relax(Instance &I, double dt, long long *n_pre, long long *n_body) {
+        long long s0 = I.nlaunch;
+        OSCAR_TRY(load_ctl(I));
+        for (int a = 0; a < I.g.dim; ++a)
+            if (cudaMemsetAsync(I.u_sum[a], 0, I.g.ncell * sizeof(double), I.stream) != cudaSuccess)
+                return OSCAR_E_CUDA;
+        cudaGraphConditionalHandle h;
+        OSCAR_TRY(cond_handle(I, &h));
+        k_relax_init<<<1, 1, 0, I.stream>>>(I.ctl, h), ++I.nlaunch;
+        *n_pre = I.nlaunch - s0;
+        cudaStream_t saved;
+        OSCAR_TRY(begin_while(I, h, &saved));
+        long long b0 = I.nlaunch, cg0 = I.cg_bodies_captured;
+        OSCAR_TRY(transport(I, I.phi_cr, dt));
+        OSCAR_TRY(interface_(I, I.alpha_new));
+        OSCAR_TRY(sum_faces(I, I.phi_vd, I.phi_cr, I.phic));
+        OSCAR_TRY(copy_fields(I, I.vold, I.u_cr, 0));
+        OSCAR_TRY(piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt));
+        OSCAR_TRY(commit_alpha(I));
+        P3<double> us;
+        for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
+        if (I.g.dim == 3)
+            k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                                                                 I.partials), ++I.nlaunch;
+        else
+            k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                                                                 I.partials), ++I.nlaunch;
+        final_sum(I, 0, S_DUMAX, true);
+        double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
+        k_relax_control<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        *n_body = (I.nlaunch - b0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
+        return end_while(I, saved);
+    }
+
+    static int build(Instance &I, int kind, double dt) {
+        GraphSlot &G = I.gslot[kind];
+        if (G.valid && G.dt == dt) return 0;
+        if (G.valid) {
+            cudaGraphExecDestroy(G.exec);
+            cudaGraphDestroy(G.graph);
+            G.valid = 0;
+        }
+        if (cudaStreamBeginCapture(I.stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) return OSCAR_E_CUDA;
+        I.capturing = 1;
+        I.depth = 0;
+        long long s0 = I.nlaunch, cg0 = I.cg_bodies_captured;
+        long long n_pre = 0, n_body = 0;
+        int rc;
+        if (kind == 0) rc = body_drag(I, dt);
+        else if (kind == 1) rc = body_relax(I, dt, &n_pre, &n_body);
+        else rc = body_standard(I, dt);
+        if (kind != 1) n_pre = (I.nlaunch - s0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(I.stream, &graph);
+        I.capturing = 0;
+        if (rc || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc ? rc : OSCAR_E_CUDA;
+        }
+        if (cudaGraphInstantiate(&G.exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return OSCAR_E_CUDA;
+        }
+        G.graph = graph;
+        G.dt = dt;
+        G.valid = 1;
+        G.n_pre = n_pre;
+        G.n_body = n_body;
+        return 0;
+    }
+
+    // Launch graph `kind` and read its control words back.
+    static int run(Instance &I, int kind, double dt, int N) {
+        OSCAR_TRY(build(I, kind, dt));
+        OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
+        for (int q = 0; q < C_COUNT; ++q) I.ctl_host[q] = 0;
+        I.ctl_host[C_N] = N;
+        if (cudaGraphLaunch(I.gslot[kind].exec, I.stream) != cudaSuccess) return OSCAR_E_CUDA;
+        if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(I.ctl_host, I.ctl, C_COUNT * sizeof(int), cudaMemcpyDeviceToHost, I.stream) !=
+                cudaSuccess)
+            return OSCAR_E_CUDA;
+        OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));
+        const GraphSlot &G = I.gslot[kind];
+        int its = I.ctl_host[C_ITSUM];
+        int trips = kind == 1 ? I.ctl_host[C_K] : 1;
+        I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body;
+        I.cg_iters_last = its;
+        I.cg_iters_total += its;
+        I.cell_updates += (long long)trips * I.n_fluid;
+        I.last_dt = dt;
+        if (I.ctl_host[C_NAN]) return OSCAR_E_NAN;
+        return I.ctl_host[C_NOTCONV] ? OSCAR_E_NOT_CONVERGED : 0;
+    }
+};
+
+template <typename T> void Solver<T>::release_graphs(Instance &I) {
+    for (int k = 0; k < 3; ++k) {
+        GraphSlot &G = I.gslot[k];
+        if (G.valid) {
+            cudaGraphExecDestroy(G.exec);
+            cudaGraphDestroy(G.graph);
+            G.valid = 0;
+        }
+    }
+}
+
+template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev, const double *alpha0_dev) {
+    GridD g = to_dev(I.g);
+    int nb = nblk(g.ncell);
+    if (I.g.dim == 3) k_build_info<3><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    else k_build_info<2><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    k_load_alpha<T><<<nb, BS, 0, I.stream>>>(g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
+    for (int l = 1; l < I.nlev; ++l) {
+        Level &F = I.lev[l - 1], &L = I.lev[l];
+        k_mg_fluid_coarsen<<<nblk(L.g.ncell), BS, 0, I.stream>>>(to_dev(F.g), to_dev(L.g), F.r[0], F.r[1], F.r[2],
+                                                                 F.fluid, L.fluid), ++I.nlaunch;
+    }
+    OSCAR_LAUNCH_CHECK();
+    long long l0 = I.nlaunch;
+    int rc = Impl<T>::interface_(I, I.alpha);
+    I.nexec += I.nlaunch;
+    (void)l0;
+    return rc;
+}
+
+template <typename T> int Solver<T>::drag_step(Instance &I, double dt) { return Impl<T>::run(I, 0, dt, 1); }
+
+template <typename T> int Solver<T>::relax(Instance &I, double dt, int N, int *kf_out, double *test_out) {
+    int rc = Impl<T>::run(I, 1, dt, N);
+    if (rc == OSCAR_E_CUDA || rc == OSCAR_E_TIMEOUT) return rc;
+    I.last_kf = I.ctl_host[C_K];
+    I.last_N = N;
+    I.last_E = I.scal_host[S_E];
+    I.last_dU = I.scal_host[S_DU];
+    if (kf_out) *kf_out = I.last_kf;
+    if (test_out) *test_out = I.scal_host[S_TEST];
+    return rc;
+}
+
+template <typename T> int Solver<T>::standard_step(Instance &I, double dt) {
+    int rc = Impl<T>::run(I, 2, dt, 1);
+    if (rc == OSCAR_E_CUDA || rc == OSCAR_E_TIMEOUT) return rc;
+    I.last_E = I.scal_host[S_E];
+    I.last_N = 1;
+    return rc;
+}
+
+// eager launches of one kernel class on the current state, timed with events
+template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int reps, double *avg_ms) {
+    using X = Impl<T>;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OSCAR_E_CUDA;
+    GridD g = to_dev(I.g);
+    int nb = nblk(g.ncell);
+    double dt = I.last_dt > 0 ? I.last_dt : 1e-7;
+    Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
+    cudaEventRecord(e0, I.stream);
+    for (int r = 0; r < reps; ++r) {
+        if (kid == OSCAR_KID_RBGS0) {
+            if (I.g.dim == 3) X::template smooth_level<3>(I, 0, r & 1); else X::template smooth_level<2>(I, 0, r & 1);
+        } else if (kid == OSCAR_KID_RESID0) {
+            if (I.g.dim == 3) X::template residual_level<3>(I, 0); else X::template residual_level<2>(I, 0);
+        } else if (kid == OSCAR_KID_CG_APPLY) {
+            if (I.g.dim == 3)
+                k_cg_apply_dot<3, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), I.cg_p, I.cg_Ap,
+                                                                      I.partials), ++I.nlaunch;
+            else
+                k_cg_apply_dot<2, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), I.cg_p, I.cg_Ap,
+                                                                      I.partials), ++I.nlaunch;
+        } else if (kid == OSCAR_KID_MOMENTUM) {
+            C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
+            if (I.g.dim == 3)
+                k_momentum_H<3, T><<<nb, BS, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold), X::c3(I.phic),
+                                                            (const T *)I.alpha_new, (const T *)I.rA, fl, T(0), (T)dt,
+                                                            Gc0, Gc1, Gc2, X::p3(I.hbya)), ++I.nlaunch;
+            else
+                k_momentum_H<2, T><<<nb, BS, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold), X::c3(I.phic),
+                                                            (const T *)I.alpha_new, (const T *)I.rA, fl, T(0), (T)dt,
+                                                            Gc0, Gc1, Gc2, X::p3(I.hbya)), ++I.nlaunch;
+        } else if (kid == OSCAR_KID_TRANSPORT) {
+            X::transport(I, I.phi_cr, dt);
+        } else {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return OSCAR_E_INVALID_ARG;
+        }
+    }
+    cudaEventRecord(e1, I.stream);
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    float ms = 0.f;
+    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = OSCAR_E_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) rc = OSCAR_E_CUDA;
+    *avg_ms = reps > 0 ? ms / reps : 0.0;
+    return rc;
+}
+
+template <typename T>
+__global__ void k_report_u(int n, const T *__restrict__ uvd, const double *__restrict__ usum, double invN,
+                           double *__restrict__ out) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[c] = (double)uvd[c] + usum[c] * invN;
+}
+static __global__ void k_add_pd(int n, const double *__restrict__ a, const double *__restrict__ b,
+                                double *__restrict__ out) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[c] = a[c] + b[c];
+}
+
+template <typename T> int Solver<T>::field_to_device(Instance &I, int which, double *dst, size_t n) {
+    int nc = I.g.ncell;
+    cudaStream_t s = I.stream;
+    auto cvt = [&](const void *src, size_t len) {
+        k_convert<T, double><<<nblk(len), BS, 0, s>>>((int)len, (const T *)src, dst), ++I.nlaunch, ++I.nexec;
+    };
+    if (which == OSCAR_FIELD_ALPHA) cvt(I.alpha, nc);
+    else if (which == OSCAR_FIELD_P) k_add_pd<<<nblk(nc), BS, 0, s>>>(nc, I.p_vd, I.p_cr, dst), ++I.nlaunch, ++I.nexec;
+    else if (which >= 2 && which <= 4) {
+        int a = which - 2;
+        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
+        else k_report_u<T><<<nblk(nc), BS, 0, s>>>(nc, (const T *)I.u_vd[a], I.u_sum[a], 1.0 / (double)I.last_N, dst),
+                 ++I.nlaunch, ++I.nexec;
+    } else if (which >= 5 && which <= 10) {
+        int a = (which - 5) % 3;
+        void *const *src = which < 8 ? I.u_vd : I.u_cr;
+        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
+        else cvt(src[a], nc);
+    } else if (which == OSCAR_FIELD_P_VD) cudaMemcpyAsync(dst, I.p_vd, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else if (which == OSCAR_FIELD_P_CR) cudaMemcpyAsync(dst, I.p_cr, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else if (which == OSCAR_FIELD_KAPPA) cvt(I.kappa, nc);
+    else if (which >= 14 && which <= 22) {
+        int a = (which - 14) % 3;
+        void *const *src = which < 17 ? I.phi_vd : (which < 20 ? I.phi_cr : I.nf);
+        if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
+        else cvt(src[a], I.g.nf[a]);
+    } else return OSCAR_E_INVALID_ARG;
+    OSCAR_LAUNCH_CHECK();
+    return 0;
+}
+
+template <typename T> int Solver<T>::field_from_device(Instance &I, int which, const double *src, size_t n) {
+    int nc = I.g.ncell;
+    cudaStream_t s = I.stream;
+    auto cvt = [&](void *dst, size_t len) {
+        k_convert<double, T><<<nblk(len), BS, 0, s>>>((int)len, src, (T *)dst), ++I.nlaunch, ++I.nexec;
+    };
+    if (which == OSCAR_FIELD_ALPHA) {
+        k_load_alpha<T><<<nblk(nc), BS, 0, s>>>(nc, I.info, src, (T *)I.alpha), ++I.nlaunch, ++I.nexec;
+        OSCAR_LAUNCH_CHECK();
+        long long l0 = I.nlaunch;
+        int rc = Impl<T>::interface_(I, I.alpha);
+        I.nexec += I.nlaunch - l0;
+        return rc;
+    } else if (which >= 5 && which <= 10) {
+        int a = (which - 5) % 3;
+        if (a >= I.g.dim) return OSCAR_E_INVALID_ARG;
+        cvt(which < 8 ? I.u_vd[a] : I.u_cr[a], nc);
+    } else if (which == OSCAR_FIELD_P_VD || which == OSCAR_FIELD_P) {
+        cudaMemcpyAsync(I.p_vd, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else if (which == OSCAR_FIELD_P_CR) {
+        cudaMemcpyAsync(I.p_cr, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    } else if (which >= 14 && which <= 19) {
+        int a = (which - 14) % 3;
+        if (a >= I.g.dim) return OSCAR_E_INVALID_ARG;
+        cvt(which < 17 ? I.phi_vd[a] : I.phi_cr[a], I.g.nf[a]);
+    } else return OSCAR_E_INVALID_ARG;
+    OSCAR_LAUNCH_CHECK();
+    return 0;
+}
+
+template <typename T> int Solver<T>::phase_volume(Instance &I, double *out) {
+    k_sum_field<T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const T *)I.alpha, I.g.V, I.partials), ++I.nlaunch,
+        ++I.nexec;
+    k_final<<<1, 1024, 0, I.stream>>>(I.partials, kRedBlocks, I.scal + S_VOL, 0), ++I.nlaunch, ++I.nexec;
+    OSCAR_LAUNCH_CHECK();
+    if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) != cudaSuccess)
+        return OSCAR_E_CUDA;
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    *out = I.scal_host[S_VOL];
+    return 0;
+}
+
+}  // namespace oscar

@@ -53,7 +53,7 @@ class oscar_stats_t(C.Structure):
 
 EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", "oscar_standard_step",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
-           "oscar_strerror", "oscar_profile", "oscar_profile_read"]
+           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel"]
 KID_RBGS0, KID_CG_APPLY, KID_MOMENTUM, KID_TRANSPORT, KID_RESID0 = range(5)
 
 _lib = None
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.oscar_strerror.restype = C.c_char_p
     lib.oscar_profile.argtypes = [H, C.c_int]
     lib.oscar_profile_read.argtypes = [H, C.c_int, dp, C.POINTER(C.c_longlong), C.c_int]
+    lib.oscar_profile_kernel.argtypes = [H, C.c_int, C.c_int, dp]
     _lib = lib
     return lib
 
@@ -191,6 +192,12 @@ class Oscar:
         _check(self.lib.oscar_profile_read(self.h, kid, C.byref(ms), C.byref(n), 1 if reset else 0),
                "oscar_profile_read")
         return ms.value, n.value
+
+    def profile_kernel(self, kid: int, reps: int = 100) -> float:
+        """Mean device time [ms] of one launch of kernel class kid (CUDA events)."""
+        ms = C.c_double(0.0)
+        _check(self.lib.oscar_profile_kernel(self.h, kid, reps, C.byref(ms)), "oscar_profile_kernel")
+        return ms.value
 
     def stats(self) -> dict:
         st = oscar_stats_t()

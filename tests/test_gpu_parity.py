@@ -137,7 +137,7 @@ def test_fp64_bubble_channel_full_run_matches_oracle():
     """The 128x16 bubble channel: 20 drag steps, each followed by up to 50
     relaxation sub-steps (tolerance 1e-6 on max |du_cr|/U), and 2000 standard
     steps at the relaxation time-step; every field within 1e-10 relative."""
-    c = inputs.channel_bubble_2d()
+    c = inputs.channel_bubble_2d(cg_rtol=1e-15, cg_maxit=400)   # oracle: exact banded solves
     dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"])
     assert N == 50
     g, o, kg, ko = run_oscar_pair(c, c.meta["n_drag"], N, dt_vd, dt_vd / N)
@@ -163,7 +163,7 @@ def _bubble_velocity(st, is_oracle):
                                   lambda: inputs.random_small_case(5, 20, 12, nz=10, dim=3)])
 def test_mixed_precision_within_tolerance(make):
     c = make()
-    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0, cg_rtol=1e-8)   # the bench's tolerance
     dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta.get("c_cfl", 0.02))
     g, o, kg, ko = run_oscar_pair(c, 3, min(N, 10), dt_vd, dt_vd / N, precision=inputs.PREC_MIXED, N=min(N, 10))
     da = np.abs(g.field(ox.FIELD_ALPHA) - o.field(oracle.ALPHA)).max()
@@ -195,7 +195,8 @@ def test_full_size_invariants(which):
     """At the bench's full sizes (mixed precision): alpha stays in [0, 1], face
     fluxes are divergence-free to the solver tolerance, the phase volume
     changes only by what crosses inlet and outlet, and nothing is non-finite."""
-    c = inputs.constricted_channel_3d() if which == "constriction_3d" else inputs.micromodel_2d()
+    c = (inputs.constricted_channel_3d(cg_rtol=1e-8) if which == "constriction_3d"
+         else inputs.micromodel_2d(cg_rtol=1e-8))
     p = c.params
     dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"])
     g = ox.Oscar(p, c.solid, c.alpha0)

@@ -102,6 +102,23 @@ def test_cg_matches_dense_cholesky(dim):
     assert np.abs(r).max() < 1e-11 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("dim,shape", [(2, (11, 9)), (2, (5, 23)), (3, (7, 6, 5)), (3, (4, 9, 6))])
+def test_banded_cholesky_matches_dense(dim, shape):
+    """The exact banded solve (shortest axis numbered fastest) equals the dense
+    Cholesky solve of the same operator."""
+    rng = np.random.default_rng(sum(shape))
+    if dim == 2:
+        case = inputs.random_small_case(40 + shape[0], shape[1], shape[0])
+    else:
+        case = inputs.random_small_case(50 + shape[0], shape[2], shape[1], nz=shape[0], dim=3)
+    p, s = case.params, case.solid
+    cf = _coeffs(p, s, rng)
+    b = rng.standard_normal(s.shape) * (s == 0)
+    qd = oracle.stage_poisson_dense(p, s, cf, b)
+    qb = oracle.stage_poisson_banded(p, s, cf, b)
+    assert np.abs(qb - qd).max() <= 1e-12 * np.abs(qd).max()
+
+
 def _manufactured_error(n):
     """-d2p/dx2 = k^2 p with p = cos(k x), k = pi/(2L): p'(0)=0 at the inlet,
     p(L) = 0 at the outlet (Dirichlet on the face), walls in y."""
