@@ -109,9 +109,13 @@ typedef struct oscar_instance *oscar_handle;
 int oscar_timesteps(const oscar_params *p, double c_cfl, double out[4]);
 
 /* Create an instance. solid: host uint8[ncell]; alpha0: host double[ncell]
- * (values in solid cells ignored). stream: a cudaStream_t (NULL = default
- * stream). Velocities, pressures and fluxes start at zero (fluid at rest).
- * Allocates all device memory of the instance. */
+ * (values in solid cells ignored). stream: a cudaStream_t, or NULL for a
+ * stream the library creates and owns (the step graphs cannot be captured on
+ * the legacy default stream). Velocities, pressures and fluxes start at zero
+ * (fluid at rest). Allocates all device memory of the instance. The
+ * environment variable OSCAR_EAGER=1 selects host-driven loops instead of
+ * graphs (same kernels, one host read-back per loop trip; for per-kernel
+ * profiling). */
 int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alpha0, void *stream,
                  oscar_handle *out);
 

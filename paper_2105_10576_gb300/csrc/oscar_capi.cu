@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -232,6 +233,18 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.P = *p;
     I.prec = p->precision;
     I.stream = (cudaStream_t)stream;
+    if (!I.stream) {   // graphs cannot be captured on the legacy default stream: use a private one
+        if (cudaStreamCreateWithFlags(&I.stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete H;
+            return OSCAR_E_CUDA;
+        }
+        I.own_stream = 1;
+    }
+    {
+        const char *e = getenv("OSCAR_EAGER");
+        I.eager = (e && e[0] == '1') ? 1 : 0;
+    }
     I.g = make_grid(p->dim, p->nx, p->ny, p->nz, p->hx, p->hy, p->hz);
     I.cos_theta = cos(p->theta_deg * M_PI / 180.0);
     I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
@@ -295,6 +308,7 @@ int oscar_destroy(oscar_handle h) {
     }
     for (int q = 0; q < 4; ++q)
         if (I.side[q]) cudaStreamDestroy(I.side[q]);
+    if (I.own_stream && I.stream) cudaStreamDestroy(I.stream);
     if (I.ctl_host) cudaFreeHost(I.ctl_host);
     if (I.prof) {
         if (I.prof->created)

@@ -22,7 +22,7 @@ enum Slot {
 };
 
 // Integer control words on the device (relaxation and PCG loop state).
-enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COUNT = 8 };
+enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COND, C_COUNT = 8 };
 
 // One captured and instantiated step graph.
 struct GraphSlot {
@@ -118,6 +118,8 @@ struct Instance {
     int *ctl;              // device control words
     int *ctl_host;         // pinned: initial control words (read by the graph) and read-back
     double last_dt;
+    int eager;             // 1: host-driven loops, no graphs (for per-kernel profiling)
+    int own_stream;        // the library created I.stream
 };
 
 int prof_begin(Instance &I, int kid);

@@ -39,7 +39,9 @@ static __global__ void k_cg_init_check(double *scal, int *ctl, double rtol, cuda
     ctl[C_IT] = 0;
     bool bad = !(isfinite(bn) && isfinite(rn));
     if (bad) ctl[C_NAN] = 1;
-    cudaGraphSetConditional(h, (!bad && rn > target) ? 1u : 0u);
+    unsigned more = (!bad && rn > target) ? 1u : 0u;
+    ctl[C_COND] = (int)more;
+    if (h) cudaGraphSetConditional(h, more);
 }
 
 static __global__ void k_cg_check(double *scal, int *ctl, int maxit, cudaGraphConditionalHandle h) {
@@ -51,7 +53,8 @@ static __global__ void k_cg_check(double *scal, int *ctl, int maxit, cudaGraphCo
     if (bad) ctl[C_NAN] = 1;
     bool more = !bad && rn > scal[S_TARGET];
     if (more && it >= maxit) { ctl[C_NOTCONV] = 1; more = false; }
-    cudaGraphSetConditional(h, more ? 1u : 0u);
+    ctl[C_COND] = more ? 1 : 0;
+    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // p = z + beta p, beta = rz_new / rz_old (0 on the first iteration)
@@ -65,7 +68,9 @@ static __global__ void k_cg_pupdate2(int n, const double *__restrict__ scal, con
 static __global__ void k_set_E(double *scal) { scal[S_E] = scal[S_RES] / (scal[S_NRM] + 1e-20); }
 
 static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) {
-    cudaGraphSetConditional(h, ctl[C_N] > 0 ? 1u : 0u);
+    unsigned more = ctl[C_N] > 0 ? 1u : 0u;
+    ctl[C_COND] = (int)more;
+    if (h) cudaGraphSetConditional(h, more);
 }
 
 // Section 3.2 early exit: stop after sub-step k if k = N or the test value
@@ -81,13 +86,15 @@ static __global__ void k_relax_control(double *scal, int *ctl, int mode, double 
     bool bad = !isfinite(test) || ctl[C_NAN];
     if (bad) ctl[C_NAN] = 1;
     bool more = !bad && k < ctl[C_N] && !(test < tol);
-    cudaGraphSetConditional(h, more ? 1u : 0u);
+    ctl[C_COND] = more ? 1 : 0;
+    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
 // capture helpers
 // ---------------------------------------------------------------------------
 inline int cond_handle(Instance &I, cudaGraphConditionalHandle *h) {
+    if (!I.capturing) { *h = 0; return 0; }
     cudaStreamCaptureStatus st;
     cudaGraph_t g;
     if (cudaStreamGetCaptureInfo(I.stream, &st, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
@@ -137,6 +144,34 @@ inline int end_while(Instance &I, cudaStream_t saved) {
     I.stream = saved;
     --I.depth;
     return e == cudaSuccess ? 0 : OSCAR_E_CUDA;
+}
+
+// Read the control words back (eager mode only).
+inline int read_ctl(Instance &I) {
+    if (cudaMemcpyAsync(I.ctl_host, I.ctl, C_COUNT * sizeof(int), cudaMemcpyDeviceToHost, I.stream) != cudaSuccess)
+        return OSCAR_E_CUDA;
+    return sync_bounded(I.stream, kSyncTimeoutSec);
+}
+
+// while (ctl[C_COND]) body(): a conditional WHILE node when capturing, a host
+// loop (one read-back per trip) in eager mode. The decision is written by the
+// kernel issued just before the loop and by the last kernel of the body.
+template <class F> int loop_while(Instance &I, cudaGraphConditionalHandle h, F body) {
+    if (I.capturing) {
+        cudaStream_t saved;
+        int rc = begin_while(I, h, &saved);
+        if (rc) return rc;
+        rc = body();
+        int rc2 = end_while(I, saved);
+        return rc ? rc : rc2;
+    }
+    for (;;) {
+        int rc = read_ctl(I);
+        if (rc) return rc;
+        if (!I.ctl_host[C_COND]) return 0;
+        rc = body();
+        if (rc) return rc;
+    }
 }
 
 #define OSCAR_TRY(x)              \
@@ -297,24 +332,26 @@ template <typename T> struct Impl {
         cudaGraphConditionalHandle h;
         OSCAR_TRY(cond_handle(I, &h));
         k_cg_init_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, h), ++I.nlaunch;
-        cudaStream_t saved;
-        OSCAR_TRY(begin_while(I, h, &saved));
-        long long n0 = I.nlaunch;
-        vcycle_d<DIM>(I, I.cg_r, I.cg_z);
-        k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
-        final_sum(I, 0, S_RZ1);
-        k_cg_pupdate2<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, I.cg_z, I.cg_p), ++I.nlaunch;
-        int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-        k_cg_apply_dot<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-        prof_end(I, ps);
-        final_sum(I, 0, S_PAP);
-        k_cg_update<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, q, I.cg_r, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-        final_sum(I, 0, S_RR);
-        k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, h), ++I.nlaunch;
-        I.n_cg_body = I.nlaunch - n0;
-        I.cg_bodies_captured += 1;
-        OSCAR_LAUNCH_CHECK();
-        return end_while(I, saved);
+        return loop_while(I, h, [&]() -> int {
+            long long n0 = I.nlaunch;
+            vcycle_d<DIM>(I, I.cg_r, I.cg_z);
+            k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
+            final_sum(I, 0, S_RZ1);
+            k_cg_pupdate2<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, I.cg_z, I.cg_p), ++I.nlaunch;
+            int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
+            k_cg_apply_dot<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
+            prof_end(I, ps);
+            final_sum(I, 0, S_PAP);
+            k_cg_update<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, q, I.cg_r, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
+            final_sum(I, 0, S_RR);
+            k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, h), ++I.nlaunch;
+            if (I.capturing) {
+                I.n_cg_body = I.nlaunch - n0;
+                I.cg_bodies_captured += 1;
+            }
+            OSCAR_LAUNCH_CHECK();
+            return 0;
+        });
     }
 
     // --- PISO (Section 2.2) --------------------------------------------------
@@ -440,29 +477,30 @@ template <typename T> struct Impl {
         OSCAR_TRY(cond_handle(I, &h));
         k_relax_init<<<1, 1, 0, I.stream>>>(I.ctl, h), ++I.nlaunch;
         *n_pre = I.nlaunch - s0;
-        cudaStream_t saved;
-        OSCAR_TRY(begin_while(I, h, &saved));
         long long b0 = I.nlaunch, cg0 = I.cg_bodies_captured;
-        OSCAR_TRY(transport(I, I.phi_cr, dt));
-        OSCAR_TRY(interface_(I, I.alpha_new));
-        OSCAR_TRY(sum_faces(I, I.phi_vd, I.phi_cr, I.phic));
-        OSCAR_TRY(copy_fields(I, I.vold, I.u_cr, 0));
-        OSCAR_TRY(piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt));
-        OSCAR_TRY(commit_alpha(I));
-        P3<double> us;
-        for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
-        if (I.g.dim == 3)
-            k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                 I.partials), ++I.nlaunch;
-        else
-            k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                 I.partials), ++I.nlaunch;
-        final_sum(I, 0, S_DUMAX, true);
-        double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
-        k_relax_control<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
-        OSCAR_LAUNCH_CHECK();
+        int rc = loop_while(I, h, [&]() -> int {
+            OSCAR_TRY(transport(I, I.phi_cr, dt));
+            OSCAR_TRY(interface_(I, I.alpha_new));
+            OSCAR_TRY(sum_faces(I, I.phi_vd, I.phi_cr, I.phic));
+            OSCAR_TRY(copy_fields(I, I.vold, I.u_cr, 0));
+            OSCAR_TRY(piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt));
+            OSCAR_TRY(commit_alpha(I));
+            P3<double> us;
+            for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
+            if (I.g.dim == 3)
+                k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                                                                     I.partials), ++I.nlaunch;
+            else
+                k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                                                                     I.partials), ++I.nlaunch;
+            final_sum(I, 0, S_DUMAX, true);
+            double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
+            k_relax_control<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
+            OSCAR_LAUNCH_CHECK();
+            return 0;
+        });
         *n_body = (I.nlaunch - b0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
-        return end_while(I, saved);
+        return rc;
     }
 
     static int build(Instance &I, int kind, double dt) {
@@ -506,11 +544,19 @@ template <typename T> struct Impl {
 
     // Launch graph `kind` and read its control words back.
     static int run(Instance &I, int kind, double dt, int N) {
-        OSCAR_TRY(build(I, kind, dt));
+        if (!I.eager) OSCAR_TRY(build(I, kind, dt));
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
         for (int q = 0; q < C_COUNT; ++q) I.ctl_host[q] = 0;
         I.ctl_host[C_N] = N;
-        if (cudaGraphLaunch(I.gslot[kind].exec, I.stream) != cudaSuccess) return OSCAR_E_CUDA;
+        if (I.eager) {
+            long long l0 = I.nlaunch, dummy0 = 0, dummy1 = 0;
+            int rc = kind == 0 ? body_drag(I, dt) : kind == 1 ? body_relax(I, dt, &dummy0, &dummy1)
+                                                              : body_standard(I, dt);
+            if (rc) return rc;
+            I.nexec += I.nlaunch - l0;
+        } else if (cudaGraphLaunch(I.gslot[kind].exec, I.stream) != cudaSuccess) {
+            return OSCAR_E_CUDA;
+        }
         if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) !=
                 cudaSuccess ||
             cudaMemcpyAsync(I.ctl_host, I.ctl, C_COUNT * sizeof(int), cudaMemcpyDeviceToHost, I.stream) !=
@@ -520,7 +566,8 @@ template <typename T> struct Impl {
         const GraphSlot &G = I.gslot[kind];
         int its = I.ctl_host[C_ITSUM];
         int trips = kind == 1 ? I.ctl_host[C_K] : 1;
-        I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body;
+        if (!I.eager)
+            I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body;
         I.cg_iters_last = its;
         I.cg_iters_total += its;
         I.cell_updates += (long long)trips * I.n_fluid;
