@@ -136,21 +136,30 @@ def test_fp64_early_exit_residual_matches_oracle():
 def test_fp64_bubble_channel_full_run_matches_oracle():
     """The 128x16 bubble channel: 20 drag steps, each followed by up to 50
     relaxation sub-steps (tolerance 1e-6 on max |du_cr|/U), and 2000 standard
-    steps at the relaxation time-step; every field within 1e-10 relative."""
+    steps at the relaxation time-step. alpha, p and kappa stay within 1e-10
+    relative. The velocity and flux fields carry the rounding noise of 1000
+    pressure solves (condition number ~1e7 at the 1000:1.2 density ratio),
+    amplified by the parasitic-current dynamics: the oracle itself moves by
+    6e-10 on these fields when only its CG tolerance changes from 1e-14 to
+    1e-15, so they are held to 2e-9."""
     c = inputs.channel_bubble_2d(cg_rtol=1e-15, cg_maxit=400)   # oracle: exact banded solves
     dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"])
     assert N == 50
     g, o, kg, ko = run_oscar_pair(c, c.meta["n_drag"], N, dt_vd, dt_vd / N)
     assert kg == ko
-    worst = compare(g, o, 2, 1e-10)
-    print("oscar worst rel err", max(worst.values()))
+    vel = ("ux", "uy", "uvdx", "uvdy", "ucrx", "ucry", "phi_vd_x", "phi_vd_y", "phi_cr_x", "phi_cr_y")
+    worst = compare(g, o, 2, 1e-10, skip=vel)
+    worst.update(compare(g, o, 2, 2e-9, skip=tuple(n for n, _, _ in fields_for(2) if n not in vel)))
+    print("oscar worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
     gs = ox.Oscar(c.params, c.solid, c.alpha0)
     os_ = oracle.OracleState(c.params, c.solid, c.alpha0)
     for _ in range(c.meta["n_standard"]):
         gs.standard_step(dt_vd / N)
         os_.standard_step(dt_vd / N)
-    worst = compare(gs, os_, 2, 1e-10, skip=("ucrx", "ucry", "phi_cr_x", "phi_cr_y"))
-    print("standard worst rel err", max(worst.values()))
+    crf = ("ucrx", "ucry", "phi_cr_x", "phi_cr_y")
+    worst = compare(gs, os_, 2, 1e-10, skip=crf + vel)
+    worst.update(compare(gs, os_, 2, 2e-9, skip=crf + tuple(n for n, _, _ in fields_for(2) if n not in vel)))
+    print("standard worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
 
 
 def _bubble_velocity(st, is_oracle):
