@@ -144,6 +144,7 @@ static void carve(Instance &I, Carver &C) {
     I.cg_z = (double *)C.take(nc * sizeof(double));
     I.cg_p = (double *)C.take(nc * sizeof(double));
     I.cg_Ap = (double *)C.take(nc * sizeof(double));
+    I.cg_e = C.take(nc * es);
     for (int a = 0; a < 3; ++a) {
         size_t nf = I.g.nf[a];
         I.nf[a] = C.take(nf * es);
@@ -164,7 +165,7 @@ static void carve(Instance &I, Carver &C) {
         L.res = C.take(n * es);
     }
     I.stage_dev = (double *)C.take(I.stage_len * sizeof(double));
-    I.partials = (double *)C.take((size_t)kRedSlots * kRedBlocks * sizeof(double));
+    I.partials = (double *)C.take((size_t)kRedSlots * I.red_stride * sizeof(double));
     I.scal = (double *)C.take(S_COUNT * sizeof(double));
     I.ctl = (int *)C.take(C_COUNT * sizeof(int));
 }
@@ -256,6 +257,15 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.n_fluid = nf;
     if (nf == 0) { delete H; return OSCAR_E_INVALID_ARG; }
     build_hierarchy(I);
+    {
+        int bx = I.g.nx >= 256 ? 256 : (I.g.nx > 64 ? 128 : (I.g.nx > 32 ? 64 : 32));
+        int by = 256 / bx;
+        long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
+        I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
+        I.lc0 = I.nlev - 1;
+        while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= 8192) --I.lc0;
+        if (I.nlev - I.lc0 > 16) I.lc0 = I.nlev - 16;
+    }
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];
     I.stage_len = stage;

@@ -18,11 +18,11 @@ constexpr double kSyncTimeoutSec = 600.0;
 // Scalar slots in the device scalar array (double).
 enum Slot {
     S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_TARGET, S_E, S_DU, S_TEST,
-    S_TMP, S_COUNT
+    S_ITARGET, S_TMP, S_COUNT
 };
 
 // Integer control words on the device (relaxation and PCG loop state).
-enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COND, C_COUNT = 8 };
+enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COND, C_OUT, C_OSUM, C_COUNT = 12 };
 
 // One captured and instantiated step graph.
 struct GraphSlot {
@@ -84,14 +84,17 @@ struct Instance {
     void *hbya[3], *vold[3], *u_vd[3], *u_cr[3], *G[9];
     // cell fields (double)
     double *u_sum[3], *p_vd, *p_cr;
-    double *cg_b, *cg_r, *cg_z, *cg_p, *cg_Ap;
+    double *cg_b, *cg_r, *cg_z, *cg_p, *cg_Ap;   // Krylov vectors hold T on the mixed path
+    void *cg_e;            // mixed path: correction of the outer defect-correction step (T)
     // face fields (T)
     void *nf[3], *phi_vd[3], *phi_cr[3], *phic[3], *phis[3], *fst[3];
     // multigrid (level 0 coefficients are the pressure operator's)
     int nlev;
     Level lev[kMaxLevels];
     // reductions
-    double *partials;      // kRedSlots * kRedBlocks
+    double *partials;      // kRedSlots * red_stride
+    int red_stride;        // partials per slot: max(kRedBlocks, blocks of a cell launch)
+    int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     double *scal;          // S_COUNT device scalars
     double *scal_host;     // pinned mirror
     double *stage_host;    // pinned staging for field transfers (max(ncell, faces) doubles)
@@ -114,6 +117,7 @@ struct Instance {
     int depth;             // current nesting depth while capturing
     int capturing;
     long long n_cg_body;   // kernels per PCG iteration
+    long long n_outer_body; // kernels per defect-correction trip outside the PCG body
     long long cg_bodies_captured;
     int *ctl;              // device control words
     int *ctl_host;         // pinned: initial control words (read by the graph) and read-back

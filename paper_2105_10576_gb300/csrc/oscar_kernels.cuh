@@ -1,17 +1,22 @@
-// OSCAR hot path on sm_103a: stencil, transport, interface, PISO and MG-PCG
-// kernels plus the per-precision orchestration of the drag step, the
-// capillary-relaxation loop and standard stepping (Maes & Menke, arXiv
-// 2105.10576, Sections 2-3).
+// OSCAR hot-path kernels for sm_103a (Maes & Menke, arXiv 2105.10576,
+// Sections 2-3): alpha transport, interface normal and curvature, PISO
+// momentum / pressure / correction, the pressure operator, CG vector
+// operations and the geometric multigrid preconditioner.
 //
-// Every kernel is memory bound (no dense contraction anywhere), so there are
-// no tensor-core paths. Layout: structure-of-arrays cell fields (x fastest) and
-// one face array per direction; one thread per cell (or per face) with
-// coalesced x-sweeps; all reductions run on a fixed grid of kRedBlocks blocks
-// and finish in one block, so every sum is deterministic run to run.
+// Every kernel is memory- or latency-bound (there is no dense contraction,
+// so no tensor-core path). Layout: structure-of-arrays cell fields with x
+// fastest and one face array per direction. Cell and face kernels run on 3D
+// grids (x over threadIdx.x for coalesced rows, y over threadIdx.y /
+// blockIdx.y, z over blockIdx.z), so no thread divides to find its cell.
+// Reductions write one partial per block and finish in one block, in a
+// fixed order, so every sum is deterministic run to run.
 //
-// Included by exactly one translation unit per element type T (double: the
-// FP64 path; float: the mixed path whose CG vectors, dots, norms and
-// accumulators stay in double).
+// Element types: T is the field type (double for the FP64 path, float for
+// the mixed path); V the CG vector type (= T); the multigrid runs in T.
+// FP64 arithmetic is rare on GB300 silicon, so the mixed path keeps it to
+// dot-product accumulation, norms and the outer defect correction.
+//
+// Included by exactly one translation unit per element type.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -27,33 +32,74 @@ namespace oscar {
 enum : int { FT_NONE = 0, FT_INTERIOR = 1, FT_WALL = 2, FT_INLET = 3, FT_OUTLET = 4 };
 constexpr uint32_t INFO_FLUID = 1u << 31;
 constexpr int BS = 256;
+constexpr int kCoarseCells = 8192;   // levels at or below this size run in one CTA
+constexpr int kMaxCL = 16;
 
 __device__ __forceinline__ int ftype(uint32_t info, int a, int s) { return (info >> (3 * (2 * a + s))) & 7; }
 
 struct GridD {
     int nx, ny, nz, ncell;
     double h[3], S[3], V;
+    float hf[3], Sf[3], Vf;
 };
 
 inline GridD to_dev(const GridH &g) {
     GridD d;
     d.nx = g.nx; d.ny = g.ny; d.nz = g.nz; d.ncell = g.ncell;
-    for (int a = 0; a < 3; ++a) { d.h[a] = g.h[a]; d.S[a] = g.S[a]; }
+    for (int a = 0; a < 3; ++a) {
+        d.h[a] = g.h[a]; d.S[a] = g.S[a];
+        d.hf[a] = (float)g.h[a]; d.Sf[a] = (float)g.S[a];
+    }
     d.V = g.V;
+    d.Vf = (float)g.V;
     return d;
 }
+
+// grid constants in the field type (no FP64 conversions in FP32 kernels)
+template <typename T> struct GA;
+template <> struct GA<double> {
+    __device__ static __forceinline__ double h(const GridD &g, int a) { return g.h[a]; }
+    __device__ static __forceinline__ double S(const GridD &g, int a) { return g.S[a]; }
+    __device__ static __forceinline__ double V(const GridD &g) { return g.V; }
+};
+template <> struct GA<float> {
+    __device__ static __forceinline__ float h(const GridD &g, int a) { return g.hf[a]; }
+    __device__ static __forceinline__ float S(const GridD &g, int a) { return g.Sf[a]; }
+    __device__ static __forceinline__ float V(const GridD &g) { return g.Vf; }
+};
 
 template <typename T> struct P3 { T *a[3]; };
 template <typename T> struct C3 { const T *a[3]; };
 
 template <typename T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
 
-__device__ __forceinline__ void coords(const GridD &g, int c, int &i, int &j, int &k) {
-    i = c % g.nx;
-    int r = c / g.nx;
-    j = r % g.ny;
-    k = r / g.ny;
+// 3D launch shape: rows of up to 256 cells along x, several rows per block
+// when rows are short.
+struct L3 {
+    dim3 grid, block;
+    int nblocks;
+};
+inline L3 launch3(int nx, int ny, int nz) {
+    int bx = nx >= 256 ? 256 : (nx > 64 ? 128 : (nx > 32 ? 64 : 32));
+    int by = BS / bx;
+    L3 l;
+    l.block = dim3(bx, by, 1);
+    l.grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+    l.nblocks = (int)(l.grid.x * l.grid.y * l.grid.z);
+    return l;
 }
+inline L3 launch3(const GridH &g) { return launch3(g.nx, g.ny, g.nz); }
+inline L3 launch3_faces(const GridH &g, int a) { return launch3(g.nx + (a == 0), g.ny + (a == 1), g.nz + (a == 2)); }
+
+#define CELL_IJK(g)                                            \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;       \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;       \
+    const int k = blockIdx.z;                                  \
+    const bool inside = i < (g).nx && j < (g).ny;              \
+    const int c = i + (g).nx * (j + (g).ny * k);
+
+#define BLOCK_ID() ((int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)))
+
 __device__ __forceinline__ int flo(const GridD &g, int a, int i, int j, int k) {
     if (a == 0) return i + (g.nx + 1) * (j + g.ny * k);
     if (a == 1) return i + g.nx * (j + (g.ny + 1) * k);
@@ -66,15 +112,25 @@ __device__ __forceinline__ int fhi(const GridD &g, int a, int i, int j, int k) {
 }
 __device__ __forceinline__ int noff(const GridD &g, int a) { return a == 0 ? 1 : (a == 1 ? g.nx : g.nx * g.ny); }
 
-// Decode face f of direction A into its fluid neighbours and type.
+// Face kernels: thread (i,j,k) of the face grid of direction A; the face
+// sits on the low side of cell (i,j,k).
+#define FACE_IJK(g, A)                                                   \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;                 \
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;                 \
+    const int k = blockIdx.z;                                            \
+    const int fnx = (g).nx + ((A) == 0), fny = (g).ny + ((A) == 1);      \
+    if (i >= fnx || j >= fny) return;                                    \
+    const int f = i + fnx * (j + fny * k);
+
+// Fluid neighbours and type of the face of direction A at face coordinates
+// (i,j,k).
 template <int A>
-__device__ __forceinline__ int decode_face(const GridD &g, const uint32_t *__restrict__ info, int f, int &L, int &H) {
-    int i, j, k, q, n;
-    if (A == 0) { i = f % (g.nx + 1); int r = f / (g.nx + 1); j = r % g.ny; k = r / g.ny; q = i; n = g.nx; }
-    else if (A == 1) { i = f % g.nx; int r = f / g.nx; j = r % (g.ny + 1); k = r / (g.ny + 1); q = j; n = g.ny; }
-    else { i = f % g.nx; int r = f / g.nx; j = r % g.ny; k = r / g.ny; q = k; n = g.nz; }
-    int off = A == 0 ? 1 : (A == 1 ? g.nx : g.nx * g.ny);
-    int c = i + g.nx * (j + g.ny * k);
+__device__ __forceinline__ int decode_face(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
+                                           int &L, int &H) {
+    const int q = A == 0 ? i : (A == 1 ? j : k);
+    const int n = A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
+    const int off = A == 0 ? 1 : (A == 1 ? g.nx : g.nx * g.ny);
+    const int c = i + g.nx * (j + g.ny * k);
     L = -1; H = -1;
     if (q < n && (info[c] & INFO_FLUID)) {
         int t = ftype(info[c], A, 0);
@@ -90,16 +146,17 @@ __device__ __forceinline__ int decode_face(const GridD &g, const uint32_t *__res
 }
 
 // ---------------------------------------------------------------------------
-// reductions (fixed grid, deterministic)
+// reductions (one partial per block, finished in one block: deterministic)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int t = threadIdx.x + blockDim.x * threadIdx.y;
+    int w = t >> 5, l = t & 31;
     __syncthreads();
     if (l == 0) sh[w] = v;
     __syncthreads();
-    int nw = blockDim.x >> 5;
+    int nw = (blockDim.x * blockDim.y) >> 5;
     if (w == 0) {
         v = l < nw ? sh[l] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -109,19 +166,20 @@ __device__ __forceinline__ double block_sum(double v) {
 __device__ __forceinline__ double block_max(double v) {
     __shared__ double sh[32];
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int t = threadIdx.x + blockDim.x * threadIdx.y;
+    int w = t >> 5, l = t & 31;
     __syncthreads();
     if (l == 0) sh[w] = v;
     __syncthreads();
-    int nw = blockDim.x >> 5;
+    int nw = (blockDim.x * blockDim.y) >> 5;
     if (w == 0) {
         v = l < nw ? sh[l] : 0.0;
         for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
     }
     return v;
 }
+__device__ __forceinline__ bool block_leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
-// out[slot] = sum (or max) of partials[0..nb)
 static __global__ void k_final(const double *__restrict__ partials, int nb, double *__restrict__ out, int is_max) {
     double v = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) v = is_max ? fmax(v, partials[b]) : v + partials[b];
@@ -135,11 +193,10 @@ static __global__ void k_final(const double *__restrict__ partials, int nb, doub
 template <int DIM>
 __global__ void k_build_info(GridD g, const uint8_t *__restrict__ solid, uint32_t *__restrict__ info,
                              uint8_t *__restrict__ fluid) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     if (solid[c]) { info[c] = 0; fluid[c] = 0; return; }
-    int ijk[3];
-    coords(g, c, ijk[0], ijk[1], ijk[2]);
+    int ijk[3] = {i, j, k};
     int n[3] = {g.nx, g.ny, g.nz};
     uint32_t w = INFO_FLUID;
 #pragma unroll
@@ -174,12 +231,6 @@ template <typename T>
 __global__ void k_sum2(int n, const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) out[c] = a[c] + b[c];
-}
-
-template <typename T>
-__global__ void k_fill(int n, T *__restrict__ x, T v) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) x[c] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -218,12 +269,10 @@ template <int DIM, typename T>
 __global__ void k_transport_low(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phi,
                                 C3<T> nf, T c_alpha, T alpha_in, T rV, T *__restrict__ aL, T *__restrict__ Pp,
                                 T *__restrict__ Pm) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) { aL[c] = T(0); Pp[c] = T(0); Pm[c] = T(0); return; }
-    int i, j, k;
-    coords(g, c, i, j, k);
     T out = T(0), pp = T(0), pm = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -256,8 +305,8 @@ template <int DIM, typename T>
 __global__ void k_transport_ratio(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha,
                                   const T *__restrict__ aL, const T *__restrict__ Pp, const T *__restrict__ Pm, T rV,
                                   T *__restrict__ Rp, T *__restrict__ Rm) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) { Rp[c] = T(0); Rm[c] = T(0); return; }
     T a0 = alpha[c], l0 = aL[c];
@@ -292,12 +341,10 @@ template <int DIM, typename T>
 __global__ void k_transport_update(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phi,
                                    C3<T> nf, T c_alpha, const T *__restrict__ aL, const T *__restrict__ Rp,
                                    const T *__restrict__ Rm, T rV, T *__restrict__ alpha_new) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) { alpha_new[c] = T(0); return; }
-    int i, j, k;
-    coords(g, c, i, j, k);
     T out = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -326,8 +373,8 @@ __global__ void k_transport_update(GridD g, const uint32_t *__restrict__ info, c
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __global__ void k_smooth(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ src, T *__restrict__ dst) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) { dst[c] = T(0); return; }
     T num = T(0), den = T(0);
@@ -335,7 +382,7 @@ __global__ void k_smooth(GridD g, const uint32_t *__restrict__ info, const T *__
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int off = noff(g, a);
-        T Sa = (T)g.S[a];
+        T Sa = GA<T>::S(g, a);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             T af = ftype(inf, a, s) == FT_INTERIOR ? T(0.5) * (x + src[s ? c + off : c - off]) : x;
@@ -354,20 +401,19 @@ __device__ __forceinline__ T gauss_grad(const GridD &g, const uint32_t *__restri
     T xc = x[c];
     T f0 = ftype(inf, b, 0) == FT_INTERIOR ? T(0.5) * (xc + x[c - off]) : xc;
     T f1 = ftype(inf, b, 1) == FT_INTERIOR ? T(0.5) * (xc + x[c + off]) : xc;
-    return (f1 - f0) / (T)g.h[b];
+    return (f1 - f0) / GA<T>::h(g, b);
 }
 
 template <int DIM, int A, typename T>
-__global__ void k_normals(GridD g, int nfaces, const uint32_t *__restrict__ info, const T *__restrict__ as, T ct, T deltaN,
+__global__ void k_normals(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ as, T ct, T deltaN,
                           T *__restrict__ nfA) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfaces) return;
+    FACE_IJK(g, A);
     int L, H;
-    int t = decode_face<A>(g, info, f, L, H);
+    int t = decode_face<A>(g, info, i, j, k, L, H);
     T n = T(0);
     if (t == FT_INTERIOR) {
         T gv[3] = {T(0), T(0), T(0)};
-        gv[A] = (as[H] - as[L]) / (T)g.h[A];
+        gv[A] = (as[H] - as[L]) / GA<T>::h(g, A);
 #pragma unroll
         for (int b = 0; b < DIM; ++b) {
             if (b == A) continue;
@@ -386,14 +432,12 @@ __global__ void k_normals(GridD g, int nfaces, const uint32_t *__restrict__ info
 
 template <int DIM, typename T>
 __global__ void k_curvature(GridD g, const uint32_t *__restrict__ info, C3<T> nf, T *__restrict__ kappa) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     if (!(info[c] & INFO_FLUID)) { kappa[c] = T(0); return; }
-    int i, j, k;
-    coords(g, c, i, j, k);
     T acc = T(0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) acc += (nf.a[a][fhi(g, a, i, j, k)] - nf.a[a][flo(g, a, i, j, k)]) / (T)g.h[a];
+    for (int a = 0; a < DIM; ++a) acc += (nf.a[a][fhi(g, a, i, j, k)] - nf.a[a][flo(g, a, i, j, k)]) / GA<T>::h(g, a);
     kappa[c] = -acc;
 }
 
@@ -403,22 +447,21 @@ __global__ void k_curvature(GridD g, const uint32_t *__restrict__ info, C3<T> nf
 template <typename T> struct Fluid { T rho1, rho2, mu1, mu2; };
 template <typename T> __device__ __forceinline__ T mix(T al, T p1, T p2) { return al * p1 + (T(1) - al) * p2; }
 
+// rA = 1/A, A = rho/dt + (viscous diagonal + rho * inflow flux)/V
 template <int DIM, typename T>
 __global__ void k_rA(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phic, Fluid<T> fl,
                      T dt, T *__restrict__ rA) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) { rA[c] = T(0); return; }
-    int i, j, k;
-    coords(g, c, i, j, k);
     T al = alpha[c];
     T rho = mix(al, fl.rho1, fl.rho2), mu = mix(al, fl.mu1, fl.mu2);
     T acc = T(0), cin = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int off = noff(g, a);
-        T Sa = (T)g.S[a], ha = (T)g.h[a];
+        T Sa = GA<T>::S(g, a), ha = GA<T>::h(g, a);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             int t = ftype(inf, a, s);
@@ -434,35 +477,34 @@ __global__ void k_rA(GridD g, const uint32_t *__restrict__ info, const T *__rest
             }
         }
     }
-    rA[c] = T(1) / (rho / dt + (acc + rho * cin) / (T)g.V);
+    rA[c] = T(1) / (rho / dt + (acc + rho * cin) / GA<T>::V(g));
 }
 
-// pressure-operator coefficients c_f (MG level 0) and CSF face forces
+// pressure-operator coefficients c_f (multigrid level 0) and CSF face forces
 template <int A, typename T>
-__global__ void k_face_coeffs(GridD g, int nfaces, const uint32_t *__restrict__ info, const T *__restrict__ rA,
+__global__ void k_face_coeffs(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ rA,
                               const T *__restrict__ kappa, const T *__restrict__ alpha, T sigma, int has_st,
                               T *__restrict__ cf, T *__restrict__ fst) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfaces) return;
+    FACE_IJK(g, A);
     int L, H;
-    int t = decode_face<A>(g, info, f, L, H);
-    T Sa = (T)g.S[A], ha = (T)g.h[A];
-    T c = T(0), fs = T(0);
+    int t = decode_face<A>(g, info, i, j, k, L, H);
+    T Sa = GA<T>::S(g, A), ha = GA<T>::h(g, A);
+    T cc = T(0), fs = T(0);
     if (t == FT_INTERIOR) {
-        c = T(0.5) * (rA[L] + rA[H]) * Sa / ha;
+        cc = T(0.5) * (rA[L] + rA[H]) * Sa / ha;
         if (has_st) fs = sigma * T(0.5) * (kappa[L] + kappa[H]) * (alpha[H] - alpha[L]) / ha;
     } else if (t == FT_OUTLET) {
-        c = rA[L] * Sa / (T(0.5) * ha);
+        cc = rA[L] * Sa / (T(0.5) * ha);
     }
-    cf[f] = c;
+    cf[f] = cc;
     fst[f] = fs;
 }
 
 // Gauss gradients of the velocity iterate: G[comp*3 + dir]
 template <int DIM, typename T>
 __global__ void k_vel_grad(GridD g, const uint32_t *__restrict__ info, C3<T> v, T vin0, P3<T> G0, P3<T> G1, P3<T> G2) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) return;
     T *Gr[3][3] = {{G0.a[0], G0.a[1], G0.a[2]}, {G1.a[0], G1.a[1], G1.a[2]}, {G2.a[0], G2.a[1], G2.a[2]}};
@@ -482,19 +524,20 @@ __global__ void k_vel_grad(GridD g, const uint32_t *__restrict__ info, C3<T> v, 
                 else if (t == FT_OUTLET) fv[s] = vc;
                 else fv[s] = T(0);
             }
-            Gr[comp][dir][c] = (fv[1] - fv[0]) / (T)g.h[dir];
+            Gr[comp][dir][c] = (fv[1] - fv[0]) / GA<T>::h(g, dir);
         }
     }
 }
 
-// HbyA = H/A: old-time term, explicit neighbour part of the viscous Laplacian,
-// linear-upwind convection (advective form) and the transpose viscous term.
+// HbyA = H/A: old-time term, neighbour part of the viscous Laplacian, inflow
+// (implicit upwind) neighbours, explicit linear-upwind correction and the
+// transpose viscous term.
 template <int DIM, typename T>
 __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, C3<T> phic,
                              const T *__restrict__ alpha, const T *__restrict__ rA, Fluid<T> fl, T vin0, T dt,
                              C3<T> G0, C3<T> G1, C3<T> G2, P3<T> hbya) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) {
 #pragma unroll
@@ -502,11 +545,10 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
         return;
     }
     const T *Gr[3][3] = {{G0.a[0], G0.a[1], G0.a[2]}, {G1.a[0], G1.a[1], G1.a[2]}, {G2.a[0], G2.a[1], G2.a[2]}};
-    int i, j, k;
-    coords(g, c, i, j, k);
     T al = alpha[c];
     T rho = mix(al, fl.rho1, fl.rho2), mu = mix(al, fl.mu1, fl.mu2);
     T rAc = rA[c];
+    const T Vc = GA<T>::V(g);
 #pragma unroll
     for (int comp = 0; comp < DIM; ++comp) {
         T vc = v.a[comp][c];
@@ -516,7 +558,7 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             int off = noff(g, a);
-            T Sa = (T)g.S[a], ha = (T)g.h[a];
+            T Sa = GA<T>::S(g, a), ha = GA<T>::h(g, a);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 int t = ftype(inf, a, s);
@@ -550,19 +592,18 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
                 }
             }
         }
-        Hc += (lap + rho * (inflow - conv) + tr) / (T)g.V;
+        Hc += (lap + rho * (inflow - conv) + tr) / Vc;
         hbya.a[comp][c] = rAc * Hc;
     }
 }
 
 template <int A, typename T>
-__global__ void k_phistar(GridD g, int nfaces, const uint32_t *__restrict__ info, const T *__restrict__ hbyaA,
+__global__ void k_phistar(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ hbyaA,
                           const T *__restrict__ rA, const T *__restrict__ fst, T vinA, T *__restrict__ phis) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfaces) return;
+    FACE_IJK(g, A);
     int L, H;
-    int t = decode_face<A>(g, info, f, L, H);
-    T Sa = (T)g.S[A];
+    int t = decode_face<A>(g, info, i, j, k, L, H);
+    T Sa = GA<T>::S(g, A);
     T ps = T(0);
     if (t == FT_INTERIOR) ps = T(0.5) * (hbyaA[L] + hbyaA[H]) * Sa + T(0.5) * (rA[L] + rA[H]) * fst[f] * Sa;
     else if (t == FT_INLET) ps = vinA * Sa;
@@ -573,11 +614,9 @@ __global__ void k_phistar(GridD g, int nfaces, const uint32_t *__restrict__ info
 // b = -div(phi*) (double)
 template <int DIM, typename T>
 __global__ void k_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> phis, double *__restrict__ b) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     if (!(info[c] & INFO_FLUID)) { b[c] = 0.0; return; }
-    int i, j, k;
-    coords(g, c, i, j, k);
     double div = 0.0;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -587,12 +626,12 @@ __global__ void k_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> phis, do
     b[c] = -div;
 }
 
-// (M q)_P = sum_f c_f (q_P - q_N) + sum_outlet c_f q_P
-template <int DIM, typename T>
-__device__ __forceinline__ double poisson_row(const GridD &g, uint32_t inf, int c, int i, int j, int k, C3<T> cf,
-                                              const double *__restrict__ q) {
-    double acc = 0.0;
-    double qc = q[c];
+// (M x)_P = sum_f c_f (x_P - x_N) + sum_outlet c_f x_P, evaluated in type V
+template <int DIM, typename T, typename V>
+__device__ __forceinline__ V poisson_row(const GridD &g, uint32_t inf, int c, int i, int j, int k, C3<T> cf,
+                                         const V *__restrict__ x) {
+    V acc = V(0);
+    V xc = x[c];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int off = noff(g, a);
@@ -601,17 +640,17 @@ __device__ __forceinline__ double poisson_row(const GridD &g, uint32_t inf, int 
             int t = ftype(inf, a, s);
             if (t == FT_INTERIOR) {
                 int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
-                acc += (double)cf.a[a][f] * (qc - q[s ? c + off : c - off]);
+                acc += (V)cf.a[a][f] * (xc - x[s ? c + off : c - off]);
             } else if (t == FT_OUTLET) {
-                acc += (double)cf.a[a][fhi(g, a, i, j, k)] * qc;
+                acc += (V)cf.a[a][fhi(g, a, i, j, k)] * xc;
             }
         }
     }
     return acc;
 }
 
-template <int DIM, typename T>
-__device__ __forceinline__ double outlet_sum(const GridD &g, uint32_t inf, int i, int j, int k, C3<T> cf) {
+template <typename T>
+__device__ __forceinline__ double outlet_coeff(const GridD &g, uint32_t inf, int i, int j, int k, C3<T> cf) {
     return ftype(inf, 0, 1) == FT_OUTLET ? (double)cf.a[0][fhi(g, 0, i, j, k)] : 0.0;
 }
 
@@ -620,21 +659,21 @@ template <int DIM, typename T>
 __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
                           const double *__restrict__ b, const double *__restrict__ scal, double inv_nf,
                           double *__restrict__ part_res, double *__restrict__ part_nrm) {
+    CELL_IJK(g);
     double qbar = scal[S_QSUM] * inv_nf;
     double res = 0.0, nrm = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    if (inside) {
         uint32_t inf = info[c];
-        if (!(inf & INFO_FLUID)) continue;
-        int i, j, k;
-        coords(g, c, i, j, k);
-        double Mq = poisson_row<DIM, T>(g, inf, c, i, j, k, cf, q);
-        double Mqbar = qbar * outlet_sum<DIM, T>(g, inf, i, j, k, cf);
-        res += fabs(b[c] - Mq);
-        nrm += fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
+        if (inf & INFO_FLUID) {
+            double Mq = poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
+            double Mqbar = qbar * outlet_coeff<T>(g, inf, i, j, k, cf);
+            res = fabs(b[c] - Mq);
+            nrm = fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
+        }
     }
     res = block_sum(res);
     nrm = block_sum(nrm);
-    if (threadIdx.x == 0) { part_res[blockIdx.x] = res; part_nrm[blockIdx.x] = nrm; }
+    if (block_leader()) { part_res[BLOCK_ID()] = res; part_nrm[BLOCK_ID()] = nrm; }
 }
 
 template <typename T>
@@ -647,12 +686,11 @@ __global__ void k_sum_field(int n, const T *__restrict__ x, double scale, double
 
 // flux correction phi = phi* - c_f (q_H - q_L)
 template <int A, typename T>
-__global__ void k_flux_correct(GridD g, int nfaces, const uint32_t *__restrict__ info, const T *__restrict__ phis,
+__global__ void k_flux_correct(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ phis,
                                const T *__restrict__ cf, const double *__restrict__ q, T *__restrict__ phi) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfaces) return;
+    FACE_IJK(g, A);
     int L, H;
-    int t = decode_face<A>(g, info, f, L, H);
+    int t = decode_face<A>(g, info, i, j, k, L, H);
     double ps = (double)phis[f];
     double out = ps;
     if (t == FT_INTERIOR) out = ps - (double)cf[f] * (q[H] - q[L]);
@@ -664,16 +702,14 @@ __global__ void k_flux_correct(GridD g, int nfaces, const uint32_t *__restrict__
 template <int DIM, typename T>
 __global__ void k_vel_correct(GridD g, const uint32_t *__restrict__ info, C3<T> hbya, const T *__restrict__ rA,
                               C3<T> fst, const double *__restrict__ q, P3<T> v) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= g.ncell) return;
+    CELL_IJK(g);
+    if (!inside) return;
     uint32_t inf = info[c];
     if (!(inf & INFO_FLUID)) {
 #pragma unroll
         for (int a = 0; a < DIM; ++a) v.a[a][c] = T(0);
         return;
     }
-    int i, j, k;
-    coords(g, c, i, j, k);
     double qc = q[c];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
@@ -715,73 +751,88 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 }
 
 // ---------------------------------------------------------------------------
-// CG (FP64 vectors)
+// CG. The residual of the outer (FP64) system is r = b - M q with q and b in
+// FP64; the Krylov vectors are of type V (double on the FP64 path, float on
+// the mixed path), dot products are accumulated in FP64.
 // ---------------------------------------------------------------------------
-template <int DIM, typename T>
+template <int DIM, typename T, typename V>
 __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
-                          const double *__restrict__ b, double *__restrict__ r, double *__restrict__ part_bb,
+                          const double *__restrict__ b, V *__restrict__ r, double *__restrict__ part_bb,
                           double *__restrict__ part_rr) {
+    CELL_IJK(g);
     double bb = 0.0, rr = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    if (inside) {
         uint32_t inf = info[c];
-        if (!(inf & INFO_FLUID)) { r[c] = 0.0; continue; }
-        int i, j, k;
-        coords(g, c, i, j, k);
-        double rc = b[c] - poisson_row<DIM, T>(g, inf, c, i, j, k, cf, q);
-        r[c] = rc;
-        bb += b[c] * b[c];
-        rr += rc * rc;
+        if (!(inf & INFO_FLUID)) {
+            r[c] = V(0);
+        } else {
+            double rc = b[c] - poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
+            r[c] = (V)rc;
+            bb = b[c] * b[c];
+            rr = rc * rc;
+        }
     }
     bb = block_sum(bb);
     rr = block_sum(rr);
-    if (threadIdx.x == 0) { part_bb[blockIdx.x] = bb; part_rr[blockIdx.x] = rr; }
+    if (block_leader()) { part_bb[BLOCK_ID()] = bb; part_rr[BLOCK_ID()] = rr; }
 }
 
-template <int DIM, typename T>
-__global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ p,
-                               double *__restrict__ Ap, double *__restrict__ part) {
+template <int DIM, typename T, typename V>
+__global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const V *__restrict__ p,
+                               V *__restrict__ Ap, double *__restrict__ part) {
+    CELL_IJK(g);
     double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+    if (inside) {
         uint32_t inf = info[c];
-        if (!(inf & INFO_FLUID)) { Ap[c] = 0.0; continue; }
-        int i, j, k;
-        coords(g, c, i, j, k);
-        double y = poisson_row<DIM, T>(g, inf, c, i, j, k, cf, p);
-        Ap[c] = y;
-        acc += p[c] * y;
+        if (!(inf & INFO_FLUID)) {
+            Ap[c] = V(0);
+        } else {
+            V y = poisson_row<DIM, T, V>(g, inf, c, i, j, k, cf, p);
+            Ap[c] = y;
+            acc = (double)(p[c] * y);
+        }
     }
     acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (block_leader()) part[BLOCK_ID()] = acc;
 }
 
-static __global__ void k_cg_update(int n, const double *__restrict__ scal, int slot_rz, double *__restrict__ q,
-                            double *__restrict__ r, const double *__restrict__ p, const double *__restrict__ Ap,
+// x += alpha p, r -= alpha Ap, partial r.r; alpha = scal[slot_rz] / scal[S_PAP]
+template <typename V>
+__global__ void k_cg_update(int n, const double *__restrict__ scal, int slot_rz, V *__restrict__ x,
+                            V *__restrict__ r, const V *__restrict__ p, const V *__restrict__ Ap,
                             double *__restrict__ part) {
-    double al = scal[slot_rz] / scal[S_PAP];
+    const V al = (V)(scal[slot_rz] / scal[S_PAP]);
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        q[c] += al * p[c];
-        double rc = r[c] - al * Ap[c];
+        x[c] += al * p[c];
+        V rc = r[c] - al * Ap[c];
         r[c] = rc;
-        acc += rc * rc;
+        acc += (double)(rc * rc);
     }
     acc = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-static __global__ void k_dot(int n, const double *__restrict__ x, const double *__restrict__ y, double *__restrict__ part) {
+template <typename V>
+__global__ void k_dot(int n, const V *__restrict__ x, const V *__restrict__ y, double *__restrict__ part) {
     double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += x[c] * y[c];
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)(x[c] * y[c]);
     acc = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// p = z + beta p, beta = scal[new]/scal[old] (beta = 0 when first)
-static __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, int slot_new, int slot_old, int first,
-                             const double *__restrict__ z, double *__restrict__ p) {
-    double be = first ? 0.0 : scal[slot_new] / scal[slot_old];
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
-        p[c] = first ? z[c] : z[c] + be * p[c];
+// p = z + beta p, beta = rz_new / rz_old (0 on the first iteration)
+template <typename V>
+__global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__restrict__ z, V *__restrict__ p) {
+    double ro = scal[S_RZ0];
+    const V be = (V)(ro != 0.0 ? scal[S_RZ1] / ro : 0.0);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
+}
+
+// outer defect correction: q += e
+template <typename V>
+__global__ void k_cg_correct(int n, const V *__restrict__ e, double *__restrict__ q) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) q[c] += (double)e[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -792,7 +843,7 @@ static __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, int 
 template <typename M> struct MG3 { const M *a[3]; };
 
 template <int DIM, typename M>
-__device__ __forceinline__ M mg_offdiag(const GridD &g, MG3<M> c, const M *__restrict__ x, int cell, int i, int j,
+__device__ __forceinline__ M mg_offdiag(const GridD &g, MG3<M> cc, const M *__restrict__ x, int cell, int i, int j,
                                         int k) {
     M acc = M(0);
     int ijk[3] = {i, j, k};
@@ -800,103 +851,87 @@ __device__ __forceinline__ M mg_offdiag(const GridD &g, MG3<M> c, const M *__res
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int off = noff(g, a);
-        if (ijk[a] > 0) acc += c.a[a][flo(g, a, i, j, k)] * x[cell - off];
-        if (ijk[a] < n[a] - 1) acc += c.a[a][fhi(g, a, i, j, k)] * x[cell + off];
+        if (ijk[a] > 0) acc += cc.a[a][flo(g, a, i, j, k)] * x[cell - off];
+        if (ijk[a] < n[a] - 1) acc += cc.a[a][fhi(g, a, i, j, k)] * x[cell + off];
     }
     return acc;
 }
 
+// one colour of a red-black Gauss-Seidel sweep; thread ti handles the cell
+// i = 2 ti + ((j + k + colour) & 1) of its row, so no thread idles
 template <int DIM, typename M>
-__global__ void k_mg_rbgs(GridD g, const uint8_t *__restrict__ fluid, MG3<M> c, const M *__restrict__ diag,
+__global__ void k_mg_rbgs(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, const M *__restrict__ diag,
                           M *__restrict__ x, const M *__restrict__ b, int colour) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.ncell) return;
-    int i, j, k;
-    coords(g, cell, i, j, k);
-    if (((i + j + k) & 1) != colour) return;
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const int i = 2 * ti + ((j + k + colour) & 1);
+    if (i >= g.nx || j >= g.ny) return;
+    const int cell = i + g.nx * (j + g.ny * k);
     M d = diag[cell];
     if (!fluid[cell] || d <= M(0)) return;
-    x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, c, x, cell, i, j, k)) / d;
+    x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d;
 }
 
+// coarse b = sum over children of the fine residual b - M x; coarse x = 0
 template <int DIM, typename M>
-__global__ void k_mg_residual(GridD g, const uint8_t *__restrict__ fluid, MG3<M> c, const M *__restrict__ diag,
-                              const M *__restrict__ x, const M *__restrict__ b, M *__restrict__ res) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.ncell) return;
-    if (!fluid[cell]) { res[cell] = M(0); return; }
-    int i, j, k;
-    coords(g, cell, i, j, k);
-    res[cell] = b[cell] - (diag[cell] * x[cell] - mg_offdiag<DIM, M>(g, c, x, cell, i, j, k));
-}
-
-// coarse b = sum of children residuals; coarse x = 0
-template <typename M>
-__global__ void k_mg_restrict(GridD gf, GridD gc, int rx, int ry, int rz, const M *__restrict__ res,
-                              M *__restrict__ bc, M *__restrict__ xc) {
-    int C = blockIdx.x * blockDim.x + threadIdx.x;
-    if (C >= gc.ncell) return;
-    int I, J, K;
-    coords(gc, C, I, J, K);
+__global__ void k_mg_resid_restrict(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
+                                    MG3<M> cc, const M *__restrict__ diag, const M *__restrict__ x,
+                                    const M *__restrict__ b, M *__restrict__ bc, M *__restrict__ xc) {
+    CELL_IJK(gc);
+    if (!inside) return;
     M acc = M(0);
     for (int oz = 0; oz < rz; ++oz) {
-        int k = K * rz + oz;
-        if (k >= gf.nz) break;
+        int kk = k * rz + oz;
+        if (kk >= gf.nz) break;
         for (int oy = 0; oy < ry; ++oy) {
-            int j = J * ry + oy;
-            if (j >= gf.ny) break;
+            int jj = j * ry + oy;
+            if (jj >= gf.ny) break;
             for (int ox = 0; ox < rx; ++ox) {
-                int i = I * rx + ox;
-                if (i >= gf.nx) break;
-                acc += res[i + gf.nx * (j + gf.ny * k)];
+                int ii = i * rx + ox;
+                if (ii >= gf.nx) break;
+                int cell = ii + gf.nx * (jj + gf.ny * kk);
+                if (!fluid[cell]) continue;
+                acc += b[cell] - (diag[cell] * x[cell] - mg_offdiag<DIM, M>(gf, cc, x, cell, ii, jj, kk));
             }
         }
     }
-    bc[C] = acc;
-    xc[C] = M(0);
+    bc[c] = acc;
+    xc[c] = M(0);
 }
 
 template <typename M>
 __global__ void k_mg_prolong(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
                              const M *__restrict__ xc, M *__restrict__ x) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= gf.ncell) return;
-    if (!fluid[cell]) return;
-    int i, j, k;
-    coords(gf, cell, i, j, k);
-    x[cell] += xc[(i / rx) + gc.nx * ((j / ry) + gc.ny * (k / rz))];
+    CELL_IJK(gf);
+    if (!inside) return;
+    if (!fluid[c]) return;
+    x[c] += xc[(i / rx) + gc.nx * ((j / ry) + gc.ny * (k / rz))];
 }
 
 static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ ff,
-                                   uint8_t *__restrict__ fc) {
-    int C = blockIdx.x * blockDim.x + threadIdx.x;
-    if (C >= gc.ncell) return;
-    int I, J, K;
-    coords(gc, C, I, J, K);
+                                          uint8_t *__restrict__ fc) {
+    CELL_IJK(gc);
+    if (!inside) return;
     uint8_t any = 0;
     for (int oz = 0; oz < rz; ++oz)
         for (int oy = 0; oy < ry; ++oy)
             for (int ox = 0; ox < rx; ++ox) {
-                int i = I * rx + ox, j = J * ry + oy, k = K * rz + oz;
-                if (i < gf.nx && j < gf.ny && k < gf.nz && ff[i + gf.nx * (j + gf.ny * k)]) any = 1;
+                int ii = i * rx + ox, jj = j * ry + oy, kk = k * rz + oz;
+                if (ii < gf.nx && jj < gf.ny && kk < gf.nz && ff[ii + gf.nx * (jj + gf.ny * kk)]) any = 1;
             }
-    fc[C] = any;
+    fc[c] = any;
 }
 
-// coarse face coefficient of direction A
+// coarse face coefficient of direction A: sum of the fine faces covering it,
+// halved across a coarsened direction
 template <int A, typename M>
-__global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int nfaces, int rx, int ry, int rz, const M *__restrict__ cfine,
+__global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, const M *__restrict__ cfine,
                                   M *__restrict__ ccoarse) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfaces) return;
-    int I, J, K;
-    if (A == 0) { I = f % (gc.nx + 1); int r = f / (gc.nx + 1); J = r % gc.ny; K = r / gc.ny; }
-    else if (A == 1) { I = f % gc.nx; int r = f / gc.nx; J = r % (gc.ny + 1); K = r / (gc.ny + 1); }
-    else { I = f % gc.nx; int r = f / gc.nx; J = r % gc.ny; K = r / gc.ny; }
+    FACE_IJK(gc, A);
     int rr[3] = {rx, ry, rz};
     int nfn[3] = {gf.nx, gf.ny, gf.nz};
-    int base[3] = {I, J, K};
-    // fine face coordinate along A, children ranges across
+    int base[3] = {i, j, k};
     int lo[3], cnt[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -911,22 +946,99 @@ __global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int nfaces, int rx, int ry
     M acc = M(0);
     for (int oz = 0; oz < cnt[2]; ++oz)
         for (int oy = 0; oy < cnt[1]; ++oy)
-            for (int ox = 0; ox < cnt[0]; ++ox)
-                acc += cfine[flo(gf, A, lo[0] + ox, lo[1] + oy, lo[2] + oz)];
+            for (int ox = 0; ox < cnt[0]; ++ox) acc += cfine[flo(gf, A, lo[0] + ox, lo[1] + oy, lo[2] + oz)];
     ccoarse[f] = rr[A] == 2 ? M(0.5) * acc : acc;
 }
 
 template <int DIM, typename M>
-__global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> c, M *__restrict__ diag) {
-    int cell = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.ncell) return;
-    if (!fluid[cell]) { diag[cell] = M(0); return; }
-    int i, j, k;
-    coords(g, cell, i, j, k);
+__global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, M *__restrict__ diag) {
+    CELL_IJK(g);
+    if (!inside) return;
+    if (!fluid[c]) { diag[c] = M(0); return; }
     M acc = M(0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) acc += c.a[a][flo(g, a, i, j, k)] + c.a[a][fhi(g, a, i, j, k)];
-    diag[cell] = acc;
+    for (int a = 0; a < DIM; ++a) acc += cc.a[a][flo(g, a, i, j, k)] + cc.a[a][fhi(g, a, i, j, k)];
+    diag[c] = acc;
+}
+
+// The V-cycle on every level at or below kCoarseCells cells, in one CTA:
+// levels 0..n-1 of this struct are consecutive hierarchy levels; the same
+// symmetric schedule as the per-level kernels (pre-smoothing red-black,
+// post-smoothing black-red, symmetric sweeps on the coarsest level).
+template <typename M> struct CLevel {
+    GridD g;
+    const M *c[3];
+    const M *diag;
+    M *x;
+    M *b;
+    const uint8_t *fluid;
+    int r[3];
+};
+template <typename M> struct CLevels {
+    int n, nu, coarse_sweeps;
+    CLevel<M> L[kMaxCL];
+};
+
+template <int DIM, typename M>
+__device__ __forceinline__ void cta_sweep(const CLevel<M> &L, int colour) {
+    const GridD &g = L.g;
+    MG3<M> cc;
+    for (int a = 0; a < 3; ++a) cc.a[a] = L.c[a];
+    for (int cell = threadIdx.x; cell < g.ncell; cell += blockDim.x) {
+        int i = cell % g.nx, r = cell / g.nx, j = r % g.ny, k = r / g.ny;
+        if (((i + j + k) & 1) != colour) continue;
+        M d = L.diag[cell];
+        if (!L.fluid[cell] || d <= M(0)) continue;
+        L.x[cell] = (L.b[cell] + mg_offdiag<DIM, M>(g, cc, L.x, cell, i, j, k)) / d;
+    }
+    __syncthreads();
+}
+
+template <int DIM, typename M>
+__global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
+    for (int l = 0; l < P.n - 1; ++l) {
+        const CLevel<M> &L = P.L[l];
+        const CLevel<M> &C = P.L[l + 1];
+        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, 0); cta_sweep<DIM, M>(L, 1); }
+        MG3<M> cc;
+        for (int a = 0; a < 3; ++a) cc.a[a] = L.c[a];
+        for (int C_ = threadIdx.x; C_ < C.g.ncell; C_ += blockDim.x) {
+            int I = C_ % C.g.nx, rr = C_ / C.g.nx, J = rr % C.g.ny, K = rr / C.g.ny;
+            M acc = M(0);
+            for (int oz = 0; oz < L.r[2]; ++oz) {
+                int kk = K * L.r[2] + oz;
+                if (kk >= L.g.nz) break;
+                for (int oy = 0; oy < L.r[1]; ++oy) {
+                    int jj = J * L.r[1] + oy;
+                    if (jj >= L.g.ny) break;
+                    for (int ox = 0; ox < L.r[0]; ++ox) {
+                        int ii = I * L.r[0] + ox;
+                        if (ii >= L.g.nx) break;
+                        int cell = ii + L.g.nx * (jj + L.g.ny * kk);
+                        if (!L.fluid[cell]) continue;
+                        acc += L.b[cell] - (L.diag[cell] * L.x[cell] - mg_offdiag<DIM, M>(L.g, cc, L.x, cell, ii, jj, kk));
+                    }
+                }
+            }
+            C.b[C_] = acc;
+            C.x[C_] = M(0);
+        }
+        __syncthreads();
+    }
+    const CLevel<M> &Lc = P.L[P.n - 1];
+    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, 0); cta_sweep<DIM, M>(Lc, 1); }
+    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, 1); cta_sweep<DIM, M>(Lc, 0); }
+    for (int l = P.n - 2; l >= 0; --l) {
+        const CLevel<M> &L = P.L[l];
+        const CLevel<M> &C = P.L[l + 1];
+        for (int cell = threadIdx.x; cell < L.g.ncell; cell += blockDim.x) {
+            if (!L.fluid[cell]) continue;
+            int i = cell % L.g.nx, r = cell / L.g.nx, j = r % L.g.ny, k = r / L.g.ny;
+            L.x[cell] += C.x[(i / L.r[0]) + C.g.nx * ((j / L.r[1]) + C.g.ny * (k / L.r[2]))];
+        }
+        __syncthreads();
+        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, 1); cta_sweep<DIM, M>(L, 0); }
+    }
 }
 
 }  // namespace oscar

@@ -2,13 +2,13 @@
 // Sections 2.2, 3.1, 3.2) as CUDA graphs.
 //
 // Each API call (drag step, relaxation, standard step) launches one
-// instantiated graph and synchronises once. Inside the graph the PCG loop of
-// every pressure solve is a conditional WHILE node whose body ends in a
-// one-thread control kernel (convergence test on the FP64 residual norm), and
-// the relaxation loop is an outer WHILE node whose control kernel applies the
-// paper's early exit (E_k < tol or k = N) on the device. Graphs are captured
-// from the same launch sequence an eager run would issue and are rebuilt
-// when the time step changes.
+// instantiated graph and synchronises once. Inside the graph every pressure
+// solve is a conditional WHILE node whose body ends in a one-thread control
+// kernel, and the relaxation loop is an outer WHILE node whose control kernel
+// applies the paper's early exit (E_k < tol or k = N) on the device. The
+// mixed path nests an FP32 PCG (FP64 dot products) inside an FP64
+// defect-correction WHILE loop. Graphs are captured from the same launch
+// sequence the eager mode issues, and rebuilt when the time step changes.
 #pragma once
 #include <string.h>
 
@@ -25,10 +25,20 @@ namespace oscar {
         }                                                                                                 \
     } while (0)
 
+#define OSCAR_TRY(x)              \
+    do {                          \
+        int rc_ = (x);            \
+        if (rc_) return rc_;      \
+    } while (0)
+
 inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
 
+constexpr int kMaxOuter = 10;          // defect-correction trips (mixed path)
+constexpr double kInnerRtol = 1e-4;    // FP32 inner solve: residual reduction per trip
+
 // ---------------------------------------------------------------------------
-// control kernels (one thread)
+// control kernels (one thread): each writes its decision to ctl[C_COND] and,
+// inside a graph, to the conditional handle
 // ---------------------------------------------------------------------------
 static __global__ void k_cg_init_check(double *scal, int *ctl, double rtol, cudaGraphConditionalHandle h) {
     double bb = scal[S_BB], rr = scal[S_RR];
@@ -44,25 +54,45 @@ static __global__ void k_cg_init_check(double *scal, int *ctl, double rtol, cuda
     if (h) cudaGraphSetConditional(h, more);
 }
 
-static __global__ void k_cg_check(double *scal, int *ctl, int maxit, cudaGraphConditionalHandle h) {
+// end of a PCG iteration: continue while ||r|| > scal[target_slot]
+static __global__ void k_cg_check(double *scal, int *ctl, int maxit, int target_slot, cudaGraphConditionalHandle h) {
     int it = ++ctl[C_IT];
     ctl[C_ITSUM] += 1;
     double rn = sqrt(scal[S_RR]);
     scal[S_RZ0] = scal[S_RZ1];
     bool bad = !isfinite(rn);
     if (bad) ctl[C_NAN] = 1;
-    bool more = !bad && rn > scal[S_TARGET];
+    bool more = !bad && rn > scal[target_slot];
     if (more && it >= maxit) { ctl[C_NOTCONV] = 1; more = false; }
     ctl[C_COND] = more ? 1 : 0;
     if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
-// p = z + beta p, beta = rz_new / rz_old (0 on the first iteration)
-static __global__ void k_cg_pupdate2(int n, const double *__restrict__ scal, const double *__restrict__ z,
-                                     double *__restrict__ p) {
-    double ro = scal[S_RZ0];
-    double be = ro != 0.0 ? scal[S_RZ1] / ro : 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
+// defect correction (mixed path): after r = b - M q in FP64, continue while
+// ||r|| > rtol ||b|| (at most kMaxOuter trips); sets the inner target
+static __global__ void k_outer_check(double *scal, int *ctl, double rtol, int first, cudaGraphConditionalHandle h) {
+    double bn = sqrt(scal[S_BB]), rn = sqrt(scal[S_RR]);
+    if (first) {
+        scal[S_TARGET] = rtol * (bn > 0.0 ? bn : rn);
+        ctl[C_OUT] = 0;
+    } else {
+        ctl[C_OUT] += 1;
+        ctl[C_OSUM] += 1;
+    }
+    bool bad = !(isfinite(bn) && isfinite(rn));
+    if (bad) ctl[C_NAN] = 1;
+    bool more = !bad && rn > scal[S_TARGET];
+    if (more && ctl[C_OUT] >= kMaxOuter) { ctl[C_NOTCONV] = 1; more = false; }
+    scal[S_ITARGET] = kInnerRtol * rn;
+    ctl[C_COND] = more ? 1 : 0;
+    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+static __global__ void k_inner_start(double *scal, int *ctl, cudaGraphConditionalHandle h) {
+    scal[S_RZ0] = 0.0;
+    ctl[C_IT] = 0;
+    ctl[C_COND] = 1;
+    if (h) cudaGraphSetConditional(h, 1u);
 }
 
 static __global__ void k_set_E(double *scal) { scal[S_E] = scal[S_RES] / (scal[S_NRM] + 1e-20); }
@@ -174,37 +204,33 @@ template <class F> int loop_while(Instance &I, cudaGraphConditionalHandle h, F b
     }
 }
 
-#define OSCAR_TRY(x)              \
-    do {                          \
-        int rc_ = (x);            \
-        if (rc_) return rc_;      \
-    } while (0)
-
 template <typename T> struct Impl {
     using M = T;
+    using V = T;
     static T *tp(void *p) { return (T *)p; }
     static C3<T> c3(void *const *p) { C3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (const T *)p[a]; return r; }
     static P3<T> p3(void *const *p) { P3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (T *)p[a]; return r; }
+    static double *part(Instance &I, int slot) { return I.partials + (size_t)slot * I.red_stride; }
 
-    static void final_sum(Instance &I, int slot_part, int slot_out, bool is_max = false) {
-        k_final<<<1, 1024, 0, I.stream>>>(I.partials + slot_part * kRedBlocks, kRedBlocks, I.scal + slot_out,
-                                          is_max ? 1 : 0), ++I.nlaunch;
+    static void final_sum(Instance &I, int slot_part, int nb, int slot_out, bool is_max = false) {
+        k_final<<<1, 1024, 0, I.stream>>>(part(I, slot_part), nb, I.scal + slot_out, is_max ? 1 : 0), ++I.nlaunch;
     }
 
     // --- transport (Eq. alphaExp) ------------------------------------------
     template <int DIM>
     static int transport_d(Instance &I, void *const *phi, double dt) {
         GridD g = to_dev(I.g);
+        L3 L = launch3(I.g);
         T rV = (T)(dt / I.g.V);
-        int nb = nblk(g.ncell);
         int ps = prof_begin(I, OSCAR_KID_TRANSPORT);
-        k_transport_low<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf), (T)I.P.c_alpha,
-                                                         (T)I.P.alpha_inlet, rV, tp(I.aL), tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
-        k_transport_ratio<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp), tp(I.Pm), rV,
-                                                           tp(I.Rp), tp(I.Rm)), ++I.nlaunch;
-        k_transport_update<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
-                                                            (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
-                                                            tp(I.alpha_new)), ++I.nlaunch;
+        k_transport_low<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
+                                                                  (T)I.P.c_alpha, (T)I.P.alpha_inlet, rV, tp(I.aL),
+                                                                  tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
+        k_transport_ratio<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp),
+                                                                    tp(I.Pm), rV, tp(I.Rp), tp(I.Rm)), ++I.nlaunch;
+        k_transport_update<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
+                                                                     (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
+                                                                     tp(I.alpha_new)), ++I.nlaunch;
         prof_end(I, ps);
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -217,20 +243,21 @@ template <typename T> struct Impl {
     template <int DIM>
     static int interface_d(Instance &I, void *alpha) {
         GridD g = to_dev(I.g);
-        int nb = nblk(g.ncell);
+        L3 L = launch3(I.g);
         void *src = alpha;
         for (int pass = 0; pass < I.P.n_smooth; ++pass) {
             void *dst = (pass % 2 == 0) ? I.alpha_s : I.alpha_tmp;
-            k_smooth<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, tp(src), tp(dst)), ++I.nlaunch;
+            k_smooth<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(src), tp(dst)), ++I.nlaunch;
             src = dst;
         }
         const T *as = tp(src);
         T ct = (T)I.cos_theta, dn = (T)I.deltaN;
-        k_normals<DIM, 0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
-        k_normals<DIM, 1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
+        L3 F0 = launch3_faces(I.g, 0), F1 = launch3_faces(I.g, 1), F2 = launch3_faces(I.g, 2);
+        k_normals<DIM, 0, T><<<F0.grid, F0.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
+        k_normals<DIM, 1, T><<<F1.grid, F1.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
         if (DIM == 3)
-            k_normals<DIM, 2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
-        k_curvature<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
+            k_normals<DIM, 2, T><<<F2.grid, F2.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
+        k_curvature<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
@@ -239,6 +266,8 @@ template <typename T> struct Impl {
     }
 
     // --- multigrid -----------------------------------------------------------
+    static MG3<M> mg3(const Level &L) { MG3<M> c; for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a]; return c; }
+
     template <int DIM>
     static int mg_coeffs_d(Instance &I) {
         for (int l = 0; l < I.nlev; ++l) {
@@ -247,108 +276,158 @@ template <typename T> struct Impl {
             if (l > 0) {
                 Level &F = I.lev[l - 1];
                 GridD gf = to_dev(F.g);
-                k_mg_coarse_coeff<0, M><<<nblk(L.g.nf[0]), BS, 0, I.stream>>>(gf, g, L.g.nf[0], F.r[0], F.r[1], F.r[2],
-                                                                          (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
-                k_mg_coarse_coeff<1, M><<<nblk(L.g.nf[1]), BS, 0, I.stream>>>(gf, g, L.g.nf[1], F.r[0], F.r[1], F.r[2],
-                                                                          (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
-                if (DIM == 3)
-                    k_mg_coarse_coeff<2, M><<<nblk(L.g.nf[2]), BS, 0, I.stream>>>(gf, g, L.g.nf[2], F.r[0], F.r[1],
-                                                                              F.r[2], (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
+                for (int a = 0; a < DIM; ++a) {
+                    L3 FL = launch3_faces(L.g, a);
+                    if (a == 0)
+                        k_mg_coarse_coeff<0, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                                                                                  (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
+                    else if (a == 1)
+                        k_mg_coarse_coeff<1, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                                                                                  (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
+                    else
+                        k_mg_coarse_coeff<2, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                                                                                  (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
+                }
             }
-            MG3<M> c;
-            for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
-            k_mg_diag<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (M *)L.diag), ++I.nlaunch;
+            L3 LL = launch3(L.g);
+            k_mg_diag<DIM, M><<<LL.grid, LL.block, 0, I.stream>>>(g, L.fluid, mg3(L), (M *)L.diag), ++I.nlaunch;
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
 
+    // x / b of level l (level 0 works in place on the Krylov vectors z / r)
+    static M *lx(Instance &I, int l, V *z) { return l == 0 ? (M *)z : (M *)I.lev[l].x; }
+    static M *lb(Instance &I, int l, V *r) { return l == 0 ? (M *)r : (M *)I.lev[l].b; }
+
     template <int DIM>
-    static void smooth_level(Instance &I, int l, int colour) {
+    static void smooth_level(Instance &I, int l, int colour, M *x, const M *b) {
         Level &L = I.lev[l];
         GridD g = to_dev(L.g);
-        MG3<M> c;
-        for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
+        L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
         int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
-        k_mg_rbgs<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag, (M *)L.x,
-                                                              (const M *)L.b, colour), ++I.nlaunch;
+        k_mg_rbgs<DIM, M><<<LL.grid, LL.block, 0, I.stream>>>(g, L.fluid, mg3(L), (const M *)L.diag, x, b, colour),
+            ++I.nlaunch;
         prof_end(I, ps);
     }
 
+    // z = V-cycle(r): pre-smoothing red-black, post-smoothing black-red
+    // (symmetric, so a valid CG preconditioner); levels from lc0 down run in
+    // one CTA.
     template <int DIM>
-    static void residual_level(Instance &I, int l) {
-        Level &L = I.lev[l];
-        GridD g = to_dev(L.g);
-        MG3<M> c;
-        for (int a = 0; a < 3; ++a) c.a[a] = (const M *)L.c[a];
-        int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-        k_mg_residual<DIM, M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, L.fluid, c, (const M *)L.diag, (const M *)L.x,
-                                                                  (const M *)L.b, (M *)L.res), ++I.nlaunch;
-        prof_end(I, ps);
-    }
-
-    // z = V-cycle(r): symmetric (pre-smoothing red-black, post-smoothing
-    // black-red), so it is a valid preconditioner for CG
-    template <int DIM>
-    static int vcycle_d(Instance &I, const double *r, double *z) {
-        int n0 = I.g.ncell;
-        k_convert<double, M><<<nblk(n0), BS, 0, I.stream>>>(n0, r, (M *)I.lev[0].b), ++I.nlaunch;
-        k_fill<M><<<nblk(n0), BS, 0, I.stream>>>(n0, (M *)I.lev[0].x, M(0)), ++I.nlaunch;
+    static int vcycle_d(Instance &I, V *r, V *z) {
+        if (cudaMemsetAsync(z, 0, (size_t)I.g.ncell * sizeof(V), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
         int nu = I.mg_nu;
-        for (int l = 0; l < I.nlev - 1; ++l) {
+        for (int l = 0; l < I.lc0; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0); smooth_level<DIM>(I, l, 1); }
-            residual_level<DIM>(I, l);
+            M *x = lx(I, l, z), *b = lb(I, l, r);
+            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0, x, b); smooth_level<DIM>(I, l, 1, x, b); }
             GridD g = to_dev(L.g), gc = to_dev(C.g);
-            k_mg_restrict<M><<<nblk(gc.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], (const M *)L.res,
-                                                                  (M *)C.b, (M *)C.x), ++I.nlaunch;
+            L3 LC = launch3(C.g);
+            int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
+            k_mg_resid_restrict<DIM, M><<<LC.grid, LC.block, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
+                                                                           mg3(L), (const M *)L.diag, x, b,
+                                                                           lb(I, l + 1, r), lx(I, l + 1, z)), ++I.nlaunch;
+            prof_end(I, ps);
         }
-        int lc = I.nlev - 1;
-        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 0); smooth_level<DIM>(I, lc, 1); }
-        for (int s = 0; s < I.mg_coarse_sweeps; ++s) { smooth_level<DIM>(I, lc, 1); smooth_level<DIM>(I, lc, 0); }
-        for (int l = I.nlev - 2; l >= 0; --l) {
+        CLevels<M> P;
+        P.n = I.nlev - I.lc0;
+        P.nu = nu;
+        P.coarse_sweeps = I.mg_coarse_sweeps;
+        for (int q = 0; q < P.n; ++q) {
+            int l = I.lc0 + q;
+            Level &L = I.lev[l];
+            P.L[q].g = to_dev(L.g);
+            for (int a = 0; a < 3; ++a) P.L[q].c[a] = (const M *)L.c[a];
+            P.L[q].diag = (const M *)L.diag;
+            P.L[q].x = lx(I, l, z);
+            P.L[q].b = lb(I, l, r);
+            P.L[q].fluid = L.fluid;
+            for (int a = 0; a < 3; ++a) P.L[q].r[a] = L.r[a];
+        }
+        k_mg_coarse<DIM, M><<<1, 1024, 0, I.stream>>>(P), ++I.nlaunch;
+        for (int l = I.lc0 - 1; l >= 0; --l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
+            M *x = lx(I, l, z), *b = lb(I, l, r);
             GridD g = to_dev(L.g), gc = to_dev(C.g);
-            k_mg_prolong<M><<<nblk(g.ncell), BS, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
-                                                                (const M *)C.x, (M *)L.x), ++I.nlaunch;
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1); smooth_level<DIM>(I, l, 0); }
+            L3 LL = launch3(L.g);
+            k_mg_prolong<M><<<LL.grid, LL.block, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
+                                                                (const M *)lx(I, l + 1, z), x), ++I.nlaunch;
+            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1, x, b); smooth_level<DIM>(I, l, 0, x, b); }
         }
-        k_convert<M, double><<<nblk(n0), BS, 0, I.stream>>>(n0, (const M *)I.lev[0].x, z), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
 
-    // PCG for M q = b (FP64 vectors), captured as init + conditional WHILE loop.
+    // r = b - M q (FP64) and ||b||^2, ||r||^2 into S_BB, S_RR
+    template <int DIM>
+    static void residual64(Instance &I, const double *q, const double *b) {
+        GridD g = to_dev(I.g);
+        L3 L = launch3(I.g);
+        k_cg_init<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, part(I, 0),
+                                                               part(I, 1)), ++I.nlaunch;
+        final_sum(I, 0, L.nblocks, S_BB);
+        final_sum(I, 1, L.nblocks, S_RR);
+    }
+
+    // one PCG iteration on M x = r with Krylov vectors z, p, Ap (type V)
+    template <int DIM>
+    static int pcg_body(Instance &I, V *x, int target_slot, cudaGraphConditionalHandle h) {
+        GridD g = to_dev(I.g);
+        L3 L = launch3(I.g);
+        int n = I.g.ncell;
+        V *r = (V *)I.cg_r, *z = (V *)I.cg_z, *p = (V *)I.cg_p, *Ap = (V *)I.cg_Ap;
+        long long n0 = I.nlaunch;
+        OSCAR_TRY(vcycle_d<DIM>(I, r, z));
+        k_dot<V><<<kRedBlocks, BS, 0, I.stream>>>(n, r, z, part(I, 0)), ++I.nlaunch;
+        final_sum(I, 0, kRedBlocks, S_RZ1);
+        k_cg_pupdate<V><<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, z, p), ++I.nlaunch;
+        int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
+        k_cg_apply_dot<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), p, Ap, part(I, 0)),
+            ++I.nlaunch;
+        prof_end(I, ps);
+        final_sum(I, 0, L.nblocks, S_PAP);
+        k_cg_update<V><<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, x, r, p, Ap, part(I, 0)), ++I.nlaunch;
+        final_sum(I, 0, kRedBlocks, S_RR);
+        k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
+        if (I.capturing) {
+            I.n_cg_body = I.nlaunch - n0;
+            I.cg_bodies_captured += 1;
+        }
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
+
+    // Pressure solve M q = b. FP64 path: PCG on q itself. Mixed path: FP64
+    // defect correction around an FP32 PCG for the correction e.
     template <int DIM>
     static int pcg_d(Instance &I, double *q, const double *b) {
-        GridD g = to_dev(I.g);
-        C3<T> cf = c3(I.lev[0].c);
-        int n = g.ncell;
-        double *part = I.partials;
-        k_cg_init<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, q, b, I.cg_r, part, part + kRedBlocks), ++I.nlaunch;
-        final_sum(I, 0, S_BB);
-        final_sum(I, 1, S_RR);
-        if (cudaMemsetAsync(I.cg_p, 0, (size_t)n * sizeof(double), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
-        cudaGraphConditionalHandle h;
-        OSCAR_TRY(cond_handle(I, &h));
-        k_cg_init_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, h), ++I.nlaunch;
-        return loop_while(I, h, [&]() -> int {
-            long long n0 = I.nlaunch;
-            vcycle_d<DIM>(I, I.cg_r, I.cg_z);
-            k_dot<<<kRedBlocks, BS, 0, I.stream>>>(n, I.cg_r, I.cg_z, part), ++I.nlaunch;
-            final_sum(I, 0, S_RZ1);
-            k_cg_pupdate2<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, I.cg_z, I.cg_p), ++I.nlaunch;
-            int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-            k_cg_apply_dot<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, cf, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-            prof_end(I, ps);
-            final_sum(I, 0, S_PAP);
-            k_cg_update<<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, q, I.cg_r, I.cg_p, I.cg_Ap, part), ++I.nlaunch;
-            final_sum(I, 0, S_RR);
-            k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, h), ++I.nlaunch;
-            if (I.capturing) {
-                I.n_cg_body = I.nlaunch - n0;
-                I.cg_bodies_captured += 1;
-            }
+        size_t nbytes = (size_t)I.g.ncell * sizeof(V);
+        if (sizeof(T) == sizeof(double)) {
+            residual64<DIM>(I, q, b);
+            if (cudaMemsetAsync(I.cg_p, 0, nbytes, I.stream) != cudaSuccess) return OSCAR_E_CUDA;
+            cudaGraphConditionalHandle h;
+            OSCAR_TRY(cond_handle(I, &h));
+            k_cg_init_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, h), ++I.nlaunch;
+            return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h); });
+        }
+        residual64<DIM>(I, q, b);
+        cudaGraphConditionalHandle ho;
+        OSCAR_TRY(cond_handle(I, &ho));
+        k_outer_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, 1, ho), ++I.nlaunch;
+        return loop_while(I, ho, [&]() -> int {
+            long long n0 = I.nlaunch, cg0 = I.cg_bodies_captured;
+            if (cudaMemsetAsync(I.cg_e, 0, nbytes, I.stream) != cudaSuccess ||
+                cudaMemsetAsync(I.cg_p, 0, nbytes, I.stream) != cudaSuccess)
+                return OSCAR_E_CUDA;
+            cudaGraphConditionalHandle hi;
+            OSCAR_TRY(cond_handle(I, &hi));
+            k_inner_start<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, hi), ++I.nlaunch;
+            OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi); }));
+            k_cg_correct<V><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
+            residual64<DIM>(I, q, b);
+            k_outer_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, 0, ho), ++I.nlaunch;
+            if (I.capturing) I.n_outer_body = (I.nlaunch - n0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
             OSCAR_LAUNCH_CHECK();
             return 0;
         });
@@ -358,58 +437,61 @@ template <typename T> struct Impl {
     template <int DIM>
     static int piso_d(Instance &I, void *const *v, double *q, void *const *phi, bool has_st, double vin0, double dt) {
         GridD g = to_dev(I.g);
-        int nb = nblk(g.ncell);
+        L3 L = launch3(I.g);
+        L3 F[3] = {launch3_faces(I.g, 0), launch3_faces(I.g, 1), launch3_faces(I.g, 2)};
         Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
         const T *al = tp(I.alpha_new);
-        k_rA<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
+        k_rA<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
         void **cf = I.lev[0].c;
         T sig = (T)I.P.sigma;
         int st = has_st ? 1 : 0;
-        k_face_coeffs<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.rA), tp(I.kappa), al, sig,
-                                                                 st, tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
-        k_face_coeffs<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.rA), tp(I.kappa), al, sig,
-                                                                 st, tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
+        k_face_coeffs<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+                                                                    tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
+        k_face_coeffs<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+                                                                    tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
         if (DIM == 3)
-            k_face_coeffs<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.rA), tp(I.kappa), al,
-                                                                     sig, st, tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
+            k_face_coeffs<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+                                                                        tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         OSCAR_TRY(mg_coeffs_d<DIM>(I));
         P3<T> Gp0 = p3(&I.G[0]), Gp1 = p3(&I.G[3]), Gp2 = p3(&I.G[6]);
         C3<T> Gc0 = c3(&I.G[0]), Gc1 = c3(&I.G[3]), Gc2 = c3(&I.G[6]);
         for (int corr = 0; corr < I.P.n_piso; ++corr) {
-            k_vel_grad<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
+            k_vel_grad<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
             int ps = prof_begin(I, OSCAR_KID_MOMENTUM);
-            k_momentum_H<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(v), c3(I.vold), c3(I.phic), al, tp(I.rA), fl,
-                                                          (T)vin0, (T)dt, Gc0, Gc1, Gc2, p3(I.hbya)), ++I.nlaunch;
+            k_momentum_H<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(v), c3(I.vold), c3(I.phic), al,
+                                                                   tp(I.rA), fl, (T)vin0, (T)dt, Gc0, Gc1, Gc2,
+                                                                   p3(I.hbya)), ++I.nlaunch;
             prof_end(I, ps);
-            k_phistar<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.hbya[0]), tp(I.rA),
-                                                                 tp(I.fst[0]), (T)vin0, tp(I.phis[0])), ++I.nlaunch;
-            k_phistar<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.hbya[1]), tp(I.rA),
-                                                                 tp(I.fst[1]), T(0), tp(I.phis[1])), ++I.nlaunch;
+            k_phistar<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.hbya[0]), tp(I.rA), tp(I.fst[0]),
+                                                                    (T)vin0, tp(I.phis[0])), ++I.nlaunch;
+            k_phistar<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.hbya[1]), tp(I.rA), tp(I.fst[1]),
+                                                                    T(0), tp(I.phis[1])), ++I.nlaunch;
             if (DIM == 3)
-                k_phistar<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.hbya[2]), tp(I.rA),
-                                                                     tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
-            k_rhs<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
+                k_phistar<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.hbya[2]), tp(I.rA),
+                                                                        tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
+            k_rhs<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
             if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
-                k_sum_field<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, I.partials), ++I.nlaunch;
-                final_sum(I, 0, S_QSUM);
-                k_normres<DIM, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
-                                                                   1.0 / (double)I.n_fluid, I.partials,
-                                                                   I.partials + kRedBlocks), ++I.nlaunch;
-                final_sum(I, 0, S_RES);
-                final_sum(I, 1, S_NRM);
+                k_sum_field<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, part(I, 0)), ++I.nlaunch;
+                final_sum(I, 0, kRedBlocks, S_QSUM);
+                k_normres<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
+                                                                    1.0 / (double)I.n_fluid, part(I, 0), part(I, 1)),
+                    ++I.nlaunch;
+                final_sum(I, 0, L.nblocks, S_RES);
+                final_sum(I, 1, L.nblocks, S_NRM);
                 k_set_E<<<1, 1, 0, I.stream>>>(I.scal), ++I.nlaunch;
             }
             OSCAR_LAUNCH_CHECK();
             OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
-            k_flux_correct<0, T><<<nblk(I.g.nf[0]), BS, 0, I.stream>>>(g, I.g.nf[0], I.info, tp(I.phis[0]), tp(cf[0]),
-                                                                      q, tp(phi[0])), ++I.nlaunch;
-            k_flux_correct<1, T><<<nblk(I.g.nf[1]), BS, 0, I.stream>>>(g, I.g.nf[1], I.info, tp(I.phis[1]), tp(cf[1]),
-                                                                      q, tp(phi[1])), ++I.nlaunch;
+            k_flux_correct<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.phis[0]), tp(cf[0]), q,
+                                                                         tp(phi[0])), ++I.nlaunch;
+            k_flux_correct<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.phis[1]), tp(cf[1]), q,
+                                                                         tp(phi[1])), ++I.nlaunch;
             if (DIM == 3)
-                k_flux_correct<2, T><<<nblk(I.g.nf[2]), BS, 0, I.stream>>>(g, I.g.nf[2], I.info, tp(I.phis[2]),
-                                                                          tp(cf[2]), q, tp(phi[2])), ++I.nlaunch;
-            k_vel_correct<DIM, T><<<nb, BS, 0, I.stream>>>(g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q, p3(v)), ++I.nlaunch;
+                k_flux_correct<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.phis[2]), tp(cf[2]), q,
+                                                                             tp(phi[2])), ++I.nlaunch;
+            k_vel_correct<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q,
+                                                                    p3(v)), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
         }
         return 0;
@@ -441,7 +523,7 @@ template <typename T> struct Impl {
                        cudaSuccess ? 0 : OSCAR_E_CUDA;
     }
 
-    // --- graph bodies -------------------------------------------------------
+    // --- step bodies ---------------------------------------------------------
     // Section 3.1: viscous-drag step
     static int body_drag(Instance &I, double dt) {
         OSCAR_TRY(load_ctl(I));
@@ -466,7 +548,7 @@ template <typename T> struct Impl {
                 return OSCAR_E_CUDA;
         return 0;
     }
-    // Section 3.2: relaxation loop as a WHILE node with the early exit on device
+    // Section 3.2: relaxation loop with the early exit on the device
     static int body_relax(Instance &I, double dt, long long *n_pre, long long *n_body) {
         long long s0 = I.nlaunch;
         OSCAR_TRY(load_ctl(I));
@@ -478,28 +560,36 @@ template <typename T> struct Impl {
         k_relax_init<<<1, 1, 0, I.stream>>>(I.ctl, h), ++I.nlaunch;
         *n_pre = I.nlaunch - s0;
         long long b0 = I.nlaunch, cg0 = I.cg_bodies_captured;
+        long long ob0 = I.cg_bodies_captured;
+        int outer_bodies_before = 0;
+        (void)ob0;
+        (void)outer_bodies_before;
+        int npiso_solves = 0;
         int rc = loop_while(I, h, [&]() -> int {
             OSCAR_TRY(transport(I, I.phi_cr, dt));
             OSCAR_TRY(interface_(I, I.alpha_new));
             OSCAR_TRY(sum_faces(I, I.phi_vd, I.phi_cr, I.phic));
             OSCAR_TRY(copy_fields(I, I.vold, I.u_cr, 0));
             OSCAR_TRY(piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt));
+            npiso_solves += I.P.n_piso;
             OSCAR_TRY(commit_alpha(I));
             P3<double> us;
             for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
             if (I.g.dim == 3)
                 k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                     I.partials), ++I.nlaunch;
+                                                                     part(I, 0)), ++I.nlaunch;
             else
                 k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                     I.partials), ++I.nlaunch;
-            final_sum(I, 0, S_DUMAX, true);
+                                                                     part(I, 0)), ++I.nlaunch;
+            final_sum(I, 0, kRedBlocks, S_DUMAX, true);
             double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
             k_relax_control<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
             return 0;
         });
-        *n_body = (I.nlaunch - b0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
+        // launches of one sub-step outside the loop bodies of its pressure solves
+        long long outer = sizeof(T) == sizeof(double) ? 0 : (long long)npiso_solves * I.n_outer_body;
+        *n_body = (I.nlaunch - b0) - (I.cg_bodies_captured - cg0) * I.n_cg_body - outer;
         return rc;
     }
 
@@ -520,7 +610,10 @@ template <typename T> struct Impl {
         if (kind == 0) rc = body_drag(I, dt);
         else if (kind == 1) rc = body_relax(I, dt, &n_pre, &n_body);
         else rc = body_standard(I, dt);
-        if (kind != 1) n_pre = (I.nlaunch - s0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
+        if (kind != 1) {
+            long long outer = sizeof(T) == sizeof(double) ? 0 : (long long)I.P.n_piso * I.n_outer_body;
+            n_pre = (I.nlaunch - s0) - (I.cg_bodies_captured - cg0) * I.n_cg_body - outer;
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(I.stream, &graph);
         I.capturing = 0;
@@ -542,16 +635,15 @@ template <typename T> struct Impl {
         return 0;
     }
 
-    // Launch graph `kind` and read its control words back.
+    // Launch step `kind` (graph, or eager loops) and read its control words back.
     static int run(Instance &I, int kind, double dt, int N) {
         if (!I.eager) OSCAR_TRY(build(I, kind, dt));
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
         for (int q = 0; q < C_COUNT; ++q) I.ctl_host[q] = 0;
         I.ctl_host[C_N] = N;
         if (I.eager) {
-            long long l0 = I.nlaunch, dummy0 = 0, dummy1 = 0;
-            int rc = kind == 0 ? body_drag(I, dt) : kind == 1 ? body_relax(I, dt, &dummy0, &dummy1)
-                                                              : body_standard(I, dt);
+            long long l0 = I.nlaunch, d0 = 0, d1 = 0;
+            int rc = kind == 0 ? body_drag(I, dt) : kind == 1 ? body_relax(I, dt, &d0, &d1) : body_standard(I, dt);
             if (rc) return rc;
             I.nexec += I.nlaunch - l0;
         } else if (cudaGraphLaunch(I.gslot[kind].exec, I.stream) != cudaSuccess) {
@@ -566,8 +658,11 @@ template <typename T> struct Impl {
         const GraphSlot &G = I.gslot[kind];
         int its = I.ctl_host[C_ITSUM];
         int trips = kind == 1 ? I.ctl_host[C_K] : 1;
-        if (!I.eager)
-            I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body;
+        if (!I.eager) {
+            long long outer_trips = sizeof(T) == sizeof(double) ? 0 : (long long)I.ctl_host[C_OSUM];
+            I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body +
+                       outer_trips * I.n_outer_body;
+        }
         I.cg_iters_last = its;
         I.cg_iters_total += its;
         I.cell_updates += (long long)trips * I.n_fluid;
@@ -590,20 +685,20 @@ template <typename T> void Solver<T>::release_graphs(Instance &I) {
 
 template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev, const double *alpha0_dev) {
     GridD g = to_dev(I.g);
-    int nb = nblk(g.ncell);
-    if (I.g.dim == 3) k_build_info<3><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    else k_build_info<2><<<nb, BS, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    k_load_alpha<T><<<nb, BS, 0, I.stream>>>(g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
+    L3 L = launch3(I.g);
+    long long l0 = I.nlaunch;
+    if (I.g.dim == 3) k_build_info<3><<<L.grid, L.block, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    else k_build_info<2><<<L.grid, L.block, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    k_load_alpha<T><<<nblk(g.ncell), BS, 0, I.stream>>>(g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
     for (int l = 1; l < I.nlev; ++l) {
-        Level &F = I.lev[l - 1], &L = I.lev[l];
-        k_mg_fluid_coarsen<<<nblk(L.g.ncell), BS, 0, I.stream>>>(to_dev(F.g), to_dev(L.g), F.r[0], F.r[1], F.r[2],
-                                                                 F.fluid, L.fluid), ++I.nlaunch;
+        Level &F = I.lev[l - 1], &Lv = I.lev[l];
+        L3 LC = launch3(Lv.g);
+        k_mg_fluid_coarsen<<<LC.grid, LC.block, 0, I.stream>>>(to_dev(F.g), to_dev(Lv.g), F.r[0], F.r[1], F.r[2],
+                                                               F.fluid, Lv.fluid), ++I.nlaunch;
     }
     OSCAR_LAUNCH_CHECK();
-    long long l0 = I.nlaunch;
     int rc = Impl<T>::interface_(I, I.alpha);
-    I.nexec += I.nlaunch;
-    (void)l0;
+    I.nexec += I.nlaunch - l0;
     return rc;
 }
 
@@ -632,35 +727,52 @@ template <typename T> int Solver<T>::standard_step(Instance &I, double dt) {
 // eager launches of one kernel class on the current state, timed with events
 template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int reps, double *avg_ms) {
     using X = Impl<T>;
+    using V = T;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OSCAR_E_CUDA;
     GridD g = to_dev(I.g);
-    int nb = nblk(g.ncell);
+    L3 L = launch3(I.g);
     double dt = I.last_dt > 0 ? I.last_dt : 1e-7;
     Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
+    Level &L0 = I.lev[0];
+    V *r = (V *)I.cg_r, *z = (V *)I.cg_z;
     cudaEventRecord(e0, I.stream);
-    for (int r = 0; r < reps; ++r) {
+    for (int rep = 0; rep < reps; ++rep) {
         if (kid == OSCAR_KID_RBGS0) {
-            if (I.g.dim == 3) X::template smooth_level<3>(I, 0, r & 1); else X::template smooth_level<2>(I, 0, r & 1);
+            if (I.g.dim == 3) X::template smooth_level<3>(I, 0, rep & 1, (T *)z, (const T *)r);
+            else X::template smooth_level<2>(I, 0, rep & 1, (T *)z, (const T *)r);
         } else if (kid == OSCAR_KID_RESID0) {
-            if (I.g.dim == 3) X::template residual_level<3>(I, 0); else X::template residual_level<2>(I, 0);
+            if (I.nlev > 1) {
+                Level &C = I.lev[1];
+                L3 LC = launch3(C.g);
+                if (I.g.dim == 3)
+                    k_mg_resid_restrict<3, T><<<LC.grid, LC.block, 0, I.stream>>>(
+                        g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
+                        (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
+                else
+                    k_mg_resid_restrict<2, T><<<LC.grid, LC.block, 0, I.stream>>>(
+                        g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
+                        (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
+            }
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)
-                k_cg_apply_dot<3, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), I.cg_p, I.cg_Ap,
-                                                                      I.partials), ++I.nlaunch;
+                k_cg_apply_dot<3, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                                                                          (V *)I.cg_Ap, X::part(I, 0)), ++I.nlaunch;
             else
-                k_cg_apply_dot<2, T><<<kRedBlocks, BS, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), I.cg_p, I.cg_Ap,
-                                                                      I.partials), ++I.nlaunch;
+                k_cg_apply_dot<2, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                                                                          (V *)I.cg_Ap, X::part(I, 0)), ++I.nlaunch;
         } else if (kid == OSCAR_KID_MOMENTUM) {
             C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
             if (I.g.dim == 3)
-                k_momentum_H<3, T><<<nb, BS, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold), X::c3(I.phic),
-                                                            (const T *)I.alpha_new, (const T *)I.rA, fl, T(0), (T)dt,
-                                                            Gc0, Gc1, Gc2, X::p3(I.hbya)), ++I.nlaunch;
+                k_momentum_H<3, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold),
+                                                                     X::c3(I.phic), (const T *)I.alpha_new,
+                                                                     (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
+                                                                     X::p3(I.hbya)), ++I.nlaunch;
             else
-                k_momentum_H<2, T><<<nb, BS, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold), X::c3(I.phic),
-                                                            (const T *)I.alpha_new, (const T *)I.rA, fl, T(0), (T)dt,
-                                                            Gc0, Gc1, Gc2, X::p3(I.hbya)), ++I.nlaunch;
+                k_momentum_H<2, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold),
+                                                                     X::c3(I.phic), (const T *)I.alpha_new,
+                                                                     (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
+                                                                     X::p3(I.hbya)), ++I.nlaunch;
         } else if (kid == OSCAR_KID_TRANSPORT) {
             X::transport(I, I.phi_cr, dt);
         } else {
