@@ -94,7 +94,7 @@ static void build_hierarchy(Instance &I) {
         GridH &g = I.lev[I.nlev - 1].g;
         int *r = I.lev[I.nlev - 1].r;
         r[0] = r[1] = r[2] = 1;
-        if (g.ncell <= 64) break;
+        if (g.ncell <= 8) break;
         int n[3] = {g.nx, g.ny, g.nz};
         double hmin = 1e300;
         for (int a = 0; a < g.dim; ++a)
@@ -168,6 +168,7 @@ static void carve(Instance &I, Carver &C) {
     I.partials = (double *)C.take((size_t)kRedSlots * I.red_stride * sizeof(double));
     I.scal = (double *)C.take(S_COUNT * sizeof(double));
     I.ctl = (int *)C.take(C_COUNT * sizeof(int));
+    I.ticket = (unsigned *)C.take(sizeof(unsigned));
 }
 
 static int validate(const oscar_params *p) {
@@ -251,7 +252,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
     I.last_N = 1;
     I.mg_nu = 2;
-    I.mg_coarse_sweeps = 8;
+    I.mg_coarse_sweeps = 4;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
@@ -262,9 +263,14 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
         int by = 256 / bx;
         long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
         I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
+        int cta_cells = 1024;
+        const char *e = getenv("OSCAR_CTA_CELLS");
+        if (e) cta_cells = atoi(e) > 0 && atoi(e) <= 1024 ? atoi(e) : cta_cells;
         I.lc0 = I.nlev - 1;
-        while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= 8192) --I.lc0;
+        while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= cta_cells) --I.lc0;
         if (I.nlev - I.lc0 > 16) I.lc0 = I.nlev - 16;
+        const char *enu = getenv("OSCAR_MG_NU");
+        if (enu && atoi(enu) >= 1 && atoi(enu) <= 4) I.mg_nu = atoi(enu);
     }
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];

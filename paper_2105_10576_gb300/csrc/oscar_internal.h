@@ -18,7 +18,7 @@ constexpr double kSyncTimeoutSec = 600.0;
 // Scalar slots in the device scalar array (double).
 enum Slot {
     S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_TARGET, S_E, S_DU, S_TEST,
-    S_ITARGET, S_TMP, S_COUNT
+    S_ITARGET, S_ALPHA, S_BETA, S_TMP, S_COUNT
 };
 
 // Integer control words on the device (relaxation and PCG loop state).
@@ -95,6 +95,8 @@ struct Instance {
     double *partials;      // kRedSlots * red_stride
     int red_stride;        // partials per slot: max(kRedBlocks, blocks of a cell launch)
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
+    size_t cta_smem;       // shared memory of the coarse kernel
+    unsigned *ticket;      // block counter of the single-pass reductions (0 between kernels)
     double *scal;          // S_COUNT device scalars
     double *scal_host;     // pinned mirror
     double *stage_host;    // pinned staging for field transfers (max(ncell, faces) doubles)

@@ -32,7 +32,7 @@ namespace oscar {
 enum : int { FT_NONE = 0, FT_INTERIOR = 1, FT_WALL = 2, FT_INLET = 3, FT_OUTLET = 4 };
 constexpr uint32_t INFO_FLUID = 1u << 31;
 constexpr int BS = 256;
-constexpr int kCoarseCells = 8192;   // levels at or below this size run in one CTA
+constexpr int kCtaCells = 1024;      // levels at or below this size run in one CTA
 constexpr int kMaxCL = 16;
 
 __device__ __forceinline__ int ftype(uint32_t info, int a, int s) { return (info >> (3 * (2 * a + s))) & 7; }
@@ -180,12 +180,84 @@ __device__ __forceinline__ double block_max(double v) {
 }
 __device__ __forceinline__ bool block_leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
-static __global__ void k_final(const double *__restrict__ partials, int nb, double *__restrict__ out, int is_max) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v = is_max ? fmax(v, partials[b]) : v + partials[b];
-    v = is_max ? block_max(v) : block_sum(v);
-    if (threadIdx.x == 0) *out = v;
+// Single-pass reduction: every block stores its partial(s); the block that
+// finishes last (atomic ticket) sums all partials in block order and returns
+// true with the totals in v0 / v1 (all its threads). Deterministic, no spin.
+// Every thread of every block must call it.
+__device__ __forceinline__ bool reduce_last(double &v0, double &v1, int nv, bool is_max, double *__restrict__ part,
+                                            int stride, unsigned *__restrict__ ticket, int nb) {
+    v0 = is_max ? block_max(v0) : block_sum(v0);
+    if (nv > 1) v1 = block_sum(v1);
+    __shared__ int last_s;
+    __shared__ double tot_s[2];
+    if (block_leader()) {
+        int b = BLOCK_ID();
+        part[b] = v0;
+        if (nv > 1) part[stride + b] = v1;
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last_s = (t == (unsigned)(nb - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last_s) return false;
+    __threadfence();
+    int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = tid; b < nb; b += nt) {
+        double p0 = __ldcg(part + b);
+        s0 = is_max ? fmax(s0, p0) : s0 + p0;
+        if (nv > 1) s1 += __ldcg(part + stride + b);
+    }
+    s0 = is_max ? block_max(s0) : block_sum(s0);
+    if (nv > 1) s1 = block_sum(s1);
+    if (block_leader()) {
+        tot_s[0] = s0;
+        tot_s[1] = s1;
+        *ticket = 0u;
+    }
+    __syncthreads();
+    v0 = tot_s[0];
+    v1 = tot_s[1];
+    return true;
 }
+
+// Loop-control decisions taken by the finishing block: each writes
+// ctl[C_COND] and, inside a graph, the conditional handle.
+__device__ __forceinline__ void set_cond(int *ctl, cudaGraphConditionalHandle h, bool more) {
+    ctl[C_COND] = more ? 1 : 0;
+    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+// after r = b - M q: mode 0 = start of a plain PCG solve; 1 / 2 = first /
+// later check of the defect-correction loop (mixed path)
+constexpr int kMaxOuter = 10;          // defect-correction trips (mixed path)
+constexpr double kInnerRtol = 1e-4;    // FP32 inner solve: residual reduction per trip
+__device__ __forceinline__ void residual_control(double *scal, int *ctl, double rtol, int mode,
+                                                 cudaGraphConditionalHandle h) {
+    double bn = sqrt(scal[S_BB]), rn = sqrt(scal[S_RR]);
+    bool bad = !(isfinite(bn) && isfinite(rn));
+    if (bad) ctl[C_NAN] = 1;
+    if (mode == 0) {
+        double target = rtol * (bn > 0.0 ? bn : rn);
+        scal[S_TARGET] = target;
+        scal[S_RZ0] = 0.0;
+        ctl[C_IT] = 0;
+        set_cond(ctl, h, !bad && rn > target);
+        return;
+    }
+    if (mode == 1) {
+        scal[S_TARGET] = rtol * (bn > 0.0 ? bn : rn);
+        ctl[C_OUT] = 0;
+    } else {
+        ctl[C_OUT] += 1;
+        ctl[C_OSUM] += 1;
+    }
+    bool more = !bad && rn > scal[S_TARGET];
+    if (more && ctl[C_OUT] >= kMaxOuter) { ctl[C_NOTCONV] = 1; more = false; }
+    scal[S_ITARGET] = kInnerRtol * rn;
+    set_cond(ctl, h, more);
+}
+
 
 // ---------------------------------------------------------------------------
 // set-up
@@ -611,19 +683,19 @@ __global__ void k_phistar(GridD g, const uint32_t *__restrict__ info, const T *_
     phis[f] = ps;
 }
 
-// b = -div(phi*) (double)
+// b = -div(phi*), summed in T, stored in FP64
 template <int DIM, typename T>
 __global__ void k_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> phis, double *__restrict__ b) {
     CELL_IJK(g);
     if (!inside) return;
     if (!(info[c] & INFO_FLUID)) { b[c] = 0.0; return; }
-    double div = 0.0;
+    T div = T(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        div += -(double)phis.a[a][flo(g, a, i, j, k)];
-        div += (double)phis.a[a][fhi(g, a, i, j, k)];
+        div += -phis.a[a][flo(g, a, i, j, k)];
+        div += phis.a[a][fhi(g, a, i, j, k)];
     }
-    b[c] = -div;
+    b[c] = (double)(-div);
 }
 
 // (M x)_P = sum_f c_f (x_P - x_N) + sum_outlet c_f x_P, evaluated in type V
@@ -654,11 +726,12 @@ __device__ __forceinline__ double outlet_coeff(const GridD &g, uint32_t inf, int
     return ftype(inf, 0, 1) == FT_OUTLET ? (double)cf.a[0][fhi(g, 0, i, j, k)] : 0.0;
 }
 
-// partial sums for the normalised residual: res = |b - Mq|, nrm = |Mq - M qbar| + |b - M qbar|
+// normalised residual (Section 3.2): res = sum |b - Mq|, nrm = sum |Mq - M qbar| + |b - M qbar|;
+// the finishing block stores E = res / (nrm + 1e-20)
 template <int DIM, typename T>
 __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
-                          const double *__restrict__ b, const double *__restrict__ scal, double inv_nf,
-                          double *__restrict__ part_res, double *__restrict__ part_nrm) {
+                          const double *__restrict__ b, double *__restrict__ scal, double inv_nf,
+                          double *__restrict__ part, int stride, unsigned *__restrict__ ticket, int nb) {
     CELL_IJK(g);
     double qbar = scal[S_QSUM] * inv_nf;
     double res = 0.0, nrm = 0.0;
@@ -671,9 +744,20 @@ __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
             nrm = fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
         }
     }
-    res = block_sum(res);
-    nrm = block_sum(nrm);
-    if (block_leader()) { part_res[BLOCK_ID()] = res; part_nrm[BLOCK_ID()] = nrm; }
+    if (reduce_last(res, nrm, 2, false, part, stride, ticket, nb) && block_leader()) {
+        scal[S_RES] = res;
+        scal[S_NRM] = nrm;
+        scal[S_E] = res / (nrm + 1e-20);
+    }
+}
+
+// scal[slot] = scale * sum of x
+template <typename T>
+__global__ void k_sum_to(int n, const T *__restrict__ x, double scale, double *__restrict__ part,
+                         unsigned *__restrict__ ticket, double *__restrict__ scal, int slot) {
+    double acc = 0.0, dummy = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)x[c];
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) scal[slot] = acc * scale;
 }
 
 template <typename T>
@@ -684,18 +768,19 @@ __global__ void k_sum_field(int n, const T *__restrict__ x, double scale, double
     if (threadIdx.x == 0) part[blockIdx.x] = acc * scale;
 }
 
-// flux correction phi = phi* - c_f (q_H - q_L)
+// flux correction phi = phi* - c_f (q_H - q_L); the pressure difference is
+// taken in FP64, the rest in T
 template <int A, typename T>
 __global__ void k_flux_correct(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ phis,
                                const T *__restrict__ cf, const double *__restrict__ q, T *__restrict__ phi) {
     FACE_IJK(g, A);
     int L, H;
     int t = decode_face<A>(g, info, i, j, k, L, H);
-    double ps = (double)phis[f];
-    double out = ps;
-    if (t == FT_INTERIOR) out = ps - (double)cf[f] * (q[H] - q[L]);
-    else if (t == FT_OUTLET) out = ps - (double)cf[f] * (0.0 - q[L]);
-    phi[f] = (T)out;
+    T ps = phis[f];
+    T out = ps;
+    if (t == FT_INTERIOR) out = ps - cf[f] * (T)(q[H] - q[L]);
+    else if (t == FT_OUTLET) out = ps - cf[f] * (T)(0.0 - q[L]);
+    phi[f] = out;
 }
 
 // v = HbyA + rA * reconstruct(face accelerations)
@@ -714,8 +799,8 @@ __global__ void k_vel_correct(GridD g, const uint32_t *__restrict__ info, C3<T> 
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         int off = noff(g, a);
-        double ha = g.h[a];
-        double gs = 0.0;
+        T ha = GA<T>::h(g, a);
+        T gs = T(0);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             int t = ftype(inf, a, s);
@@ -723,20 +808,23 @@ __global__ void k_vel_correct(GridD g, const uint32_t *__restrict__ info, C3<T> 
                 int nb = s ? c + off : c - off;
                 int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
                 double qL = s ? qc : q[nb], qH = s ? q[nb] : qc;
-                gs += (double)fst.a[a][f] - (qH - qL) / ha;
+                gs += fst.a[a][f] - (T)(qH - qL) / ha;
             } else if (t == FT_OUTLET) {
-                gs += -(0.0 - qc) / (0.5 * ha);
+                gs += -(T)(0.0 - qc) / (T(0.5) * ha);
             }
         }
-        v.a[a][c] = (T)((double)hbya.a[a][c] + (double)rA[c] * 0.5 * gs);
+        v.a[a][c] = hbya.a[a][c] + rA[c] * T(0.5) * gs;
     }
 }
 
-// u_sum += v; partial max |v - vold|
+// u_sum += v and max |v - vold|; the finishing block applies the early exit
+// of Section 3.2: stop after sub-step k if k = N or the test value (E_k, or
+// max |du_cr| / U) is below the tolerance
 template <int DIM, typename T>
 __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, P3<double> usum,
-                              double *__restrict__ part) {
-    double m = 0.0;
+                              double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
+                              int *__restrict__ ctl, int mode, double tol, double invU, cudaGraphConditionalHandle h) {
+    double m = 0.0, dummy = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         if (!(info[c] & INFO_FLUID)) continue;
 #pragma unroll
@@ -746,19 +834,32 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
             m = fmax(m, fabs(x - (double)vold.a[a][c]));
         }
     }
-    m = block_max(m);
-    if (threadIdx.x == 0) part[blockIdx.x] = m;
+    if (reduce_last(m, dummy, 1, true, part, 0, ticket, gridDim.x) && block_leader()) {
+        scal[S_DUMAX] = m;
+        int k = ++ctl[C_K];
+        double E = scal[S_E];
+        double dU = m * invU;
+        double test = mode == OSCAR_CONV_DU_MAX ? dU : E;
+        scal[S_DU] = dU;
+        scal[S_TEST] = test;
+        bool bad = !isfinite(test) || ctl[C_NAN];
+        if (bad) ctl[C_NAN] = 1;
+        set_cond(ctl, h, !bad && k < ctl[C_N] && !(test < tol));
+    }
 }
 
 // ---------------------------------------------------------------------------
 // CG. The residual of the outer (FP64) system is r = b - M q with q and b in
 // FP64; the Krylov vectors are of type V (double on the FP64 path, float on
-// the mixed path), dot products are accumulated in FP64.
+// the mixed path). Dot products are accumulated per thread in V and across
+// threads and blocks in FP64; the finishing block of each reduction also
+// computes the CG scalars and takes the loop decisions.
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, typename V>
 __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
-                          const double *__restrict__ b, V *__restrict__ r, double *__restrict__ part_bb,
-                          double *__restrict__ part_rr) {
+                          const double *__restrict__ b, V *__restrict__ r, double *__restrict__ part, int stride,
+                          unsigned *__restrict__ ticket, int nb, double *__restrict__ scal, int *__restrict__ ctl,
+                          double rtol, int mode, cudaGraphConditionalHandle h) {
     CELL_IJK(g);
     double bb = 0.0, rr = 0.0;
     if (inside) {
@@ -772,16 +873,20 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
             rr = rc * rc;
         }
     }
-    bb = block_sum(bb);
-    rr = block_sum(rr);
-    if (block_leader()) { part_bb[BLOCK_ID()] = bb; part_rr[BLOCK_ID()] = rr; }
+    if (reduce_last(bb, rr, 2, false, part, stride, ticket, nb) && block_leader()) {
+        scal[S_BB] = bb;
+        scal[S_RR] = rr;
+        residual_control(scal, ctl, rtol, mode, h);
+    }
 }
 
+// Ap = M p and p.Ap; the finishing block sets alpha = (r.z) / (p.Ap)
 template <int DIM, typename T, typename V>
 __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const V *__restrict__ p,
-                               V *__restrict__ Ap, double *__restrict__ part) {
+                               V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket, int nb,
+                               double *__restrict__ scal) {
     CELL_IJK(g);
-    double acc = 0.0;
+    double acc = 0.0, dummy = 0.0;
     if (inside) {
         uint32_t inf = info[c];
         if (!(inf & INFO_FLUID)) {
@@ -792,40 +897,60 @@ __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T>
             acc = (double)(p[c] * y);
         }
     }
-    acc = block_sum(acc);
-    if (block_leader()) part[BLOCK_ID()] = acc;
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, nb) && block_leader()) {
+        scal[S_PAP] = acc;
+        scal[S_ALPHA] = scal[S_RZ1] / acc;
+    }
 }
 
-// x += alpha p, r -= alpha Ap, partial r.r; alpha = scal[slot_rz] / scal[S_PAP]
+// x += alpha p, r -= alpha Ap; the finishing block tests ||r|| against
+// scal[target_slot] and decides whether the PCG loop continues
 template <typename V>
-__global__ void k_cg_update(int n, const double *__restrict__ scal, int slot_rz, V *__restrict__ x,
-                            V *__restrict__ r, const V *__restrict__ p, const V *__restrict__ Ap,
-                            double *__restrict__ part) {
-    const V al = (V)(scal[slot_rz] / scal[S_PAP]);
-    double acc = 0.0;
+__global__ void k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
+                            const V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket,
+                            double *__restrict__ scal, int *__restrict__ ctl, int maxit, int target_slot,
+                            cudaGraphConditionalHandle h) {
+    const V al = (V)scal[S_ALPHA];
+    V accv = V(0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         x[c] += al * p[c];
         V rc = r[c] - al * Ap[c];
         r[c] = rc;
-        acc += (double)(rc * rc);
+        accv += rc * rc;
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    double acc = (double)accv, dummy = 0.0;
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) {
+        scal[S_RR] = acc;
+        int it = ++ctl[C_IT];
+        ctl[C_ITSUM] += 1;
+        double rn = sqrt(acc);
+        scal[S_RZ0] = scal[S_RZ1];
+        bool bad = !isfinite(rn);
+        if (bad) ctl[C_NAN] = 1;
+        bool more = !bad && rn > scal[target_slot];
+        if (more && it >= maxit) { ctl[C_NOTCONV] = 1; more = false; }
+        set_cond(ctl, h, more);
+    }
 }
 
+// r.z; the finishing block sets beta = (r.z)_new / (r.z)_old (0 on the first iteration)
 template <typename V>
-__global__ void k_dot(int n, const V *__restrict__ x, const V *__restrict__ y, double *__restrict__ part) {
-    double acc = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)(x[c] * y[c]);
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+__global__ void k_cg_dot_rz(int n, const V *__restrict__ x, const V *__restrict__ y, double *__restrict__ part,
+                            unsigned *__restrict__ ticket, double *__restrict__ scal) {
+    V accv = V(0);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) accv += x[c] * y[c];
+    double acc = (double)accv, dummy = 0.0;
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) {
+        double ro = scal[S_RZ0];
+        scal[S_RZ1] = acc;
+        scal[S_BETA] = ro != 0.0 ? acc / ro : 0.0;
+    }
 }
 
-// p = z + beta p, beta = rz_new / rz_old (0 on the first iteration)
+// p = z + beta p
 template <typename V>
 __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__restrict__ z, V *__restrict__ p) {
-    double ro = scal[S_RZ0];
-    const V be = (V)(ro != 0.0 ? scal[S_RZ1] / ro : 0.0);
+    const V be = (V)scal[S_BETA];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
 }
 
@@ -961,49 +1086,71 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
     diag[c] = acc;
 }
 
-// The V-cycle on every level at or below kCoarseCells cells, in one CTA:
-// levels 0..n-1 of this struct are consecutive hierarchy levels; the same
-// symmetric schedule as the per-level kernels (pre-smoothing red-black,
-// post-smoothing black-red, symmetric sweeps on the coarsest level).
+// The V-cycle on the coarse levels (at most 1024 cells each) in one CTA of
+// 1024 threads, one cell per thread, with every level held in shared memory;
+// the same symmetric schedule as the per-level kernels (pre-smoothing
+// red-black, post-smoothing black-red, symmetric sweeps on the coarsest
+// level). Reads b of its top level from global memory, writes x back.
 template <typename M> struct CLevel {
     GridD g;
-    const M *c[3];
+    const M *c[3];     // global face coefficients
     const M *diag;
-    M *x;
-    M *b;
     const uint8_t *fluid;
-    int r[3];
+    int r[3];          // ratios to the next level
+    int ox, ob, od, oc[3], ofl;   // shared-memory offsets (bytes)
 };
 template <typename M> struct CLevels {
     int n, nu, coarse_sweeps;
+    const M *b_top;    // global b of the top level
+    M *x_top;          // global x of the top level
     CLevel<M> L[kMaxCL];
 };
 
 template <int DIM, typename M>
-__device__ __forceinline__ void cta_sweep(const CLevel<M> &L, int colour) {
+__device__ __forceinline__ void cta_sweep(const CLevel<M> &L, unsigned char *sm, int colour) {
     const GridD &g = L.g;
+    M *x = (M *)(sm + L.ox);
+    const M *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
+    const uint8_t *fl = sm + L.ofl;
     MG3<M> cc;
-    for (int a = 0; a < 3; ++a) cc.a[a] = L.c[a];
-    for (int cell = threadIdx.x; cell < g.ncell; cell += blockDim.x) {
+    for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
+    int cell = threadIdx.x;
+    if (cell < g.ncell) {
         int i = cell % g.nx, r = cell / g.nx, j = r % g.ny, k = r / g.ny;
-        if (((i + j + k) & 1) != colour) continue;
-        M d = L.diag[cell];
-        if (!L.fluid[cell] || d <= M(0)) continue;
-        L.x[cell] = (L.b[cell] + mg_offdiag<DIM, M>(g, cc, L.x, cell, i, j, k)) / d;
+        if (((i + j + k) & 1) == colour && fl[cell] && d[cell] > M(0))
+            x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d[cell];
     }
     __syncthreads();
 }
 
 template <int DIM, typename M>
 __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int t = threadIdx.x;
+    for (int l = 0; l < P.n; ++l) {
+        const CLevel<M> &L = P.L[l];
+        const GridD &g = L.g;
+        int nf[3] = {(g.nx + 1) * g.ny * g.nz, g.nx * (g.ny + 1) * g.nz, g.nx * g.ny * (g.nz + 1)};
+        for (int a = 0; a < DIM; ++a)
+            for (int q = t; q < nf[a]; q += blockDim.x) ((M *)(sm + L.oc[a]))[q] = L.c[a][q];
+        if (t < g.ncell) {
+            ((M *)(sm + L.od))[t] = L.diag[t];
+            (sm + L.ofl)[t] = L.fluid[t];
+            ((M *)(sm + L.ox))[t] = M(0);
+            ((M *)(sm + L.ob))[t] = l == 0 ? P.b_top[t] : M(0);
+        }
+    }
+    __syncthreads();
     for (int l = 0; l < P.n - 1; ++l) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
-        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, 0); cta_sweep<DIM, M>(L, 1); }
+        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, sm, 0); cta_sweep<DIM, M>(L, sm, 1); }
+        const M *x = (const M *)(sm + L.ox), *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
+        const uint8_t *fl = sm + L.ofl;
         MG3<M> cc;
-        for (int a = 0; a < 3; ++a) cc.a[a] = L.c[a];
-        for (int C_ = threadIdx.x; C_ < C.g.ncell; C_ += blockDim.x) {
-            int I = C_ % C.g.nx, rr = C_ / C.g.nx, J = rr % C.g.ny, K = rr / C.g.ny;
+        for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
+        if (t < C.g.ncell) {
+            int I = t % C.g.nx, rr = t / C.g.nx, J = rr % C.g.ny, K = rr / C.g.ny;
             M acc = M(0);
             for (int oz = 0; oz < L.r[2]; ++oz) {
                 int kk = K * L.r[2] + oz;
@@ -1015,30 +1162,29 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
                         int ii = I * L.r[0] + ox;
                         if (ii >= L.g.nx) break;
                         int cell = ii + L.g.nx * (jj + L.g.ny * kk);
-                        if (!L.fluid[cell]) continue;
-                        acc += L.b[cell] - (L.diag[cell] * L.x[cell] - mg_offdiag<DIM, M>(L.g, cc, L.x, cell, ii, jj, kk));
+                        if (!fl[cell]) continue;
+                        acc += b[cell] - (d[cell] * x[cell] - mg_offdiag<DIM, M>(L.g, cc, x, cell, ii, jj, kk));
                     }
                 }
             }
-            C.b[C_] = acc;
-            C.x[C_] = M(0);
+            ((M *)(sm + C.ob))[t] = acc;
         }
         __syncthreads();
     }
     const CLevel<M> &Lc = P.L[P.n - 1];
-    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, 0); cta_sweep<DIM, M>(Lc, 1); }
-    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, 1); cta_sweep<DIM, M>(Lc, 0); }
+    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, sm, 0); cta_sweep<DIM, M>(Lc, sm, 1); }
+    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, sm, 1); cta_sweep<DIM, M>(Lc, sm, 0); }
     for (int l = P.n - 2; l >= 0; --l) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
-        for (int cell = threadIdx.x; cell < L.g.ncell; cell += blockDim.x) {
-            if (!L.fluid[cell]) continue;
-            int i = cell % L.g.nx, r = cell / L.g.nx, j = r % L.g.ny, k = r / L.g.ny;
-            L.x[cell] += C.x[(i / L.r[0]) + C.g.nx * ((j / L.r[1]) + C.g.ny * (k / L.r[2]))];
+        if (t < L.g.ncell && (sm + L.ofl)[t]) {
+            int i = t % L.g.nx, r = t / L.g.nx, j = r % L.g.ny, k = r / L.g.ny;
+            ((M *)(sm + L.ox))[t] += ((const M *)(sm + C.ox))[(i / L.r[0]) + C.g.nx * ((j / L.r[1]) + C.g.ny * (k / L.r[2]))];
         }
         __syncthreads();
-        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, 1); cta_sweep<DIM, M>(L, 0); }
+        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, sm, 1); cta_sweep<DIM, M>(L, sm, 0); }
     }
+    if (t < P.L[0].g.ncell) P.x_top[t] = ((const M *)(sm + P.L[0].ox))[t];
 }
 
 }  // namespace oscar

@@ -33,92 +33,19 @@ namespace oscar {
 
 inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
 
-constexpr int kMaxOuter = 10;          // defect-correction trips (mixed path)
-constexpr double kInnerRtol = 1e-4;    // FP32 inner solve: residual reduction per trip
 
 // ---------------------------------------------------------------------------
-// control kernels (one thread): each writes its decision to ctl[C_COND] and,
-// inside a graph, to the conditional handle
+// control kernels (one thread). The other loop decisions are taken by the
+// finishing block of the reductions (see k_cg_init, k_cg_update,
+// k_relax_accum).
 // ---------------------------------------------------------------------------
-static __global__ void k_cg_init_check(double *scal, int *ctl, double rtol, cudaGraphConditionalHandle h) {
-    double bb = scal[S_BB], rr = scal[S_RR];
-    double bn = sqrt(bb), rn = sqrt(rr);
-    double target = rtol * (bn > 0.0 ? bn : rn);
-    scal[S_TARGET] = target;
-    scal[S_RZ0] = 0.0;
-    ctl[C_IT] = 0;
-    bool bad = !(isfinite(bn) && isfinite(rn));
-    if (bad) ctl[C_NAN] = 1;
-    unsigned more = (!bad && rn > target) ? 1u : 0u;
-    ctl[C_COND] = (int)more;
-    if (h) cudaGraphSetConditional(h, more);
-}
-
-// end of a PCG iteration: continue while ||r|| > scal[target_slot]
-static __global__ void k_cg_check(double *scal, int *ctl, int maxit, int target_slot, cudaGraphConditionalHandle h) {
-    int it = ++ctl[C_IT];
-    ctl[C_ITSUM] += 1;
-    double rn = sqrt(scal[S_RR]);
-    scal[S_RZ0] = scal[S_RZ1];
-    bool bad = !isfinite(rn);
-    if (bad) ctl[C_NAN] = 1;
-    bool more = !bad && rn > scal[target_slot];
-    if (more && it >= maxit) { ctl[C_NOTCONV] = 1; more = false; }
-    ctl[C_COND] = more ? 1 : 0;
-    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
-}
-
-// defect correction (mixed path): after r = b - M q in FP64, continue while
-// ||r|| > rtol ||b|| (at most kMaxOuter trips); sets the inner target
-static __global__ void k_outer_check(double *scal, int *ctl, double rtol, int first, cudaGraphConditionalHandle h) {
-    double bn = sqrt(scal[S_BB]), rn = sqrt(scal[S_RR]);
-    if (first) {
-        scal[S_TARGET] = rtol * (bn > 0.0 ? bn : rn);
-        ctl[C_OUT] = 0;
-    } else {
-        ctl[C_OUT] += 1;
-        ctl[C_OSUM] += 1;
-    }
-    bool bad = !(isfinite(bn) && isfinite(rn));
-    if (bad) ctl[C_NAN] = 1;
-    bool more = !bad && rn > scal[S_TARGET];
-    if (more && ctl[C_OUT] >= kMaxOuter) { ctl[C_NOTCONV] = 1; more = false; }
-    scal[S_ITARGET] = kInnerRtol * rn;
-    ctl[C_COND] = more ? 1 : 0;
-    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
-}
-
 static __global__ void k_inner_start(double *scal, int *ctl, cudaGraphConditionalHandle h) {
     scal[S_RZ0] = 0.0;
     ctl[C_IT] = 0;
-    ctl[C_COND] = 1;
-    if (h) cudaGraphSetConditional(h, 1u);
+    set_cond(ctl, h, true);
 }
 
-static __global__ void k_set_E(double *scal) { scal[S_E] = scal[S_RES] / (scal[S_NRM] + 1e-20); }
-
-static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) {
-    unsigned more = ctl[C_N] > 0 ? 1u : 0u;
-    ctl[C_COND] = (int)more;
-    if (h) cudaGraphSetConditional(h, more);
-}
-
-// Section 3.2 early exit: stop after sub-step k if k = N or the test value
-// (E_k, or max |du_cr| / U) is below the tolerance.
-static __global__ void k_relax_control(double *scal, int *ctl, int mode, double tol, double invU,
-                                       cudaGraphConditionalHandle h) {
-    int k = ++ctl[C_K];
-    double E = scal[S_E];
-    double dU = scal[S_DUMAX] * invU;
-    double test = mode == OSCAR_CONV_DU_MAX ? dU : E;
-    scal[S_DU] = dU;
-    scal[S_TEST] = test;
-    bool bad = !isfinite(test) || ctl[C_NAN];
-    if (bad) ctl[C_NAN] = 1;
-    bool more = !bad && k < ctl[C_N] && !(test < tol);
-    ctl[C_COND] = more ? 1 : 0;
-    if (h) cudaGraphSetConditional(h, more ? 1u : 0u);
-}
+static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) { set_cond(ctl, h, ctl[C_N] > 0); }
 
 // ---------------------------------------------------------------------------
 // capture helpers
@@ -212,9 +139,6 @@ template <typename T> struct Impl {
     static P3<T> p3(void *const *p) { P3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (T *)p[a]; return r; }
     static double *part(Instance &I, int slot) { return I.partials + (size_t)slot * I.red_stride; }
 
-    static void final_sum(Instance &I, int slot_part, int nb, int slot_out, bool is_max = false) {
-        k_final<<<1, 1024, 0, I.stream>>>(part(I, slot_part), nb, I.scal + slot_out, is_max ? 1 : 0), ++I.nlaunch;
-    }
 
     // --- transport (Eq. alphaExp) ------------------------------------------
     template <int DIM>
@@ -296,6 +220,31 @@ template <typename T> struct Impl {
         return 0;
     }
 
+    // levels lc0.. of the single-CTA coarse kernel with their shared-memory layout
+    static size_t cta_levels(Instance &I, CLevels<M> &P) {
+        P.n = I.nlev - I.lc0;
+        P.nu = I.mg_nu;
+        P.coarse_sweeps = I.mg_coarse_sweeps;
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
+        for (int q = 0; q < P.n; ++q) {
+            Level &L = I.lev[I.lc0 + q];
+            CLevel<M> &C = P.L[q];
+            C.g = to_dev(L.g);
+            for (int a = 0; a < 3; ++a) C.c[a] = (const M *)L.c[a];
+            C.diag = (const M *)L.diag;
+            C.fluid = L.fluid;
+            for (int a = 0; a < 3; ++a) C.r[a] = L.r[a];
+            size_t n = L.g.ncell;
+            C.ox = take(n * sizeof(M));
+            C.ob = take(n * sizeof(M));
+            C.od = take(n * sizeof(M));
+            for (int a = 0; a < 3; ++a) C.oc[a] = take((size_t)L.g.nf[a] * sizeof(M));
+            C.ofl = take(n);
+        }
+        return off;
+    }
+
     // x / b of level l (level 0 works in place on the Krylov vectors z / r)
     static M *lx(Instance &I, int l, V *z) { return l == 0 ? (M *)z : (M *)I.lev[l].x; }
     static M *lb(Instance &I, int l, V *r) { return l == 0 ? (M *)r : (M *)I.lev[l].b; }
@@ -331,21 +280,10 @@ template <typename T> struct Impl {
             prof_end(I, ps);
         }
         CLevels<M> P;
-        P.n = I.nlev - I.lc0;
-        P.nu = nu;
-        P.coarse_sweeps = I.mg_coarse_sweeps;
-        for (int q = 0; q < P.n; ++q) {
-            int l = I.lc0 + q;
-            Level &L = I.lev[l];
-            P.L[q].g = to_dev(L.g);
-            for (int a = 0; a < 3; ++a) P.L[q].c[a] = (const M *)L.c[a];
-            P.L[q].diag = (const M *)L.diag;
-            P.L[q].x = lx(I, l, z);
-            P.L[q].b = lb(I, l, r);
-            P.L[q].fluid = L.fluid;
-            for (int a = 0; a < 3; ++a) P.L[q].r[a] = L.r[a];
-        }
-        k_mg_coarse<DIM, M><<<1, 1024, 0, I.stream>>>(P), ++I.nlaunch;
+        cta_levels(I, P);
+        P.b_top = lb(I, I.lc0, r);
+        P.x_top = lx(I, I.lc0, z);
+        k_mg_coarse<DIM, M><<<1, 1024, I.cta_smem, I.stream>>>(P), ++I.nlaunch;
         for (int l = I.lc0 - 1; l >= 0; --l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -359,15 +297,15 @@ template <typename T> struct Impl {
         return 0;
     }
 
-    // r = b - M q (FP64) and ||b||^2, ||r||^2 into S_BB, S_RR
+    // r = b - M q (FP64), ||b||^2, ||r||^2 into S_BB, S_RR, then the loop
+    // decision of residual_control(mode)
     template <int DIM>
-    static void residual64(Instance &I, const double *q, const double *b) {
+    static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h) {
         GridD g = to_dev(I.g);
         L3 L = launch3(I.g);
-        k_cg_init<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, part(I, 0),
-                                                               part(I, 1)), ++I.nlaunch;
-        final_sum(I, 0, L.nblocks, S_BB);
-        final_sum(I, 1, L.nblocks, S_RR);
+        k_cg_init<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, I.partials,
+                                                               I.red_stride, I.ticket, L.nblocks, I.scal, I.ctl,
+                                                               I.P.cg_rtol, mode, h), ++I.nlaunch;
     }
 
     // one PCG iteration on M x = r with Krylov vectors z, p, Ap (type V)
@@ -379,17 +317,14 @@ template <typename T> struct Impl {
         V *r = (V *)I.cg_r, *z = (V *)I.cg_z, *p = (V *)I.cg_p, *Ap = (V *)I.cg_Ap;
         long long n0 = I.nlaunch;
         OSCAR_TRY(vcycle_d<DIM>(I, r, z));
-        k_dot<V><<<kRedBlocks, BS, 0, I.stream>>>(n, r, z, part(I, 0)), ++I.nlaunch;
-        final_sum(I, 0, kRedBlocks, S_RZ1);
+        k_cg_dot_rz<V><<<kRedBlocks, BS, 0, I.stream>>>(n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
         k_cg_pupdate<V><<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, z, p), ++I.nlaunch;
         int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-        k_cg_apply_dot<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), p, Ap, part(I, 0)),
-            ++I.nlaunch;
+        k_cg_apply_dot<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), p, Ap, I.partials,
+                                                                    I.ticket, L.nblocks, I.scal), ++I.nlaunch;
         prof_end(I, ps);
-        final_sum(I, 0, L.nblocks, S_PAP);
-        k_cg_update<V><<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, S_RZ1, x, r, p, Ap, part(I, 0)), ++I.nlaunch;
-        final_sum(I, 0, kRedBlocks, S_RR);
-        k_cg_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
+        k_cg_update<V><<<kRedBlocks, BS, 0, I.stream>>>(n, x, r, p, Ap, I.partials, I.ticket, I.scal, I.ctl,
+                                                        I.P.cg_maxit, target_slot, h), ++I.nlaunch;
         if (I.capturing) {
             I.n_cg_body = I.nlaunch - n0;
             I.cg_bodies_captured += 1;
@@ -403,18 +338,16 @@ template <typename T> struct Impl {
     template <int DIM>
     static int pcg_d(Instance &I, double *q, const double *b) {
         size_t nbytes = (size_t)I.g.ncell * sizeof(V);
-        if (sizeof(T) == sizeof(double)) {
-            residual64<DIM>(I, q, b);
+        if constexpr (sizeof(T) == sizeof(double)) {
             if (cudaMemsetAsync(I.cg_p, 0, nbytes, I.stream) != cudaSuccess) return OSCAR_E_CUDA;
             cudaGraphConditionalHandle h;
             OSCAR_TRY(cond_handle(I, &h));
-            k_cg_init_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, h), ++I.nlaunch;
+            residual64<DIM>(I, q, b, 0, h);
             return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h); });
-        }
-        residual64<DIM>(I, q, b);
+        } else {
         cudaGraphConditionalHandle ho;
         OSCAR_TRY(cond_handle(I, &ho));
-        k_outer_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, 1, ho), ++I.nlaunch;
+        residual64<DIM>(I, q, b, 1, ho);
         return loop_while(I, ho, [&]() -> int {
             long long n0 = I.nlaunch, cg0 = I.cg_bodies_captured;
             if (cudaMemsetAsync(I.cg_e, 0, nbytes, I.stream) != cudaSuccess ||
@@ -425,12 +358,12 @@ template <typename T> struct Impl {
             k_inner_start<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, hi), ++I.nlaunch;
             OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi); }));
             k_cg_correct<V><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
-            residual64<DIM>(I, q, b);
-            k_outer_check<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.cg_rtol, 0, ho), ++I.nlaunch;
+            residual64<DIM>(I, q, b, 2, ho);
             if (I.capturing) I.n_outer_body = (I.nlaunch - n0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
             OSCAR_LAUNCH_CHECK();
             return 0;
         });
+        }
     }
 
     // --- PISO (Section 2.2) --------------------------------------------------
@@ -472,14 +405,11 @@ template <typename T> struct Impl {
                                                                         tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
             k_rhs<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
             if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
-                k_sum_field<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, part(I, 0)), ++I.nlaunch;
-                final_sum(I, 0, kRedBlocks, S_QSUM);
+                k_sum_to<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
+                                                                  S_QSUM), ++I.nlaunch;
                 k_normres<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
-                                                                    1.0 / (double)I.n_fluid, part(I, 0), part(I, 1)),
-                    ++I.nlaunch;
-                final_sum(I, 0, L.nblocks, S_RES);
-                final_sum(I, 1, L.nblocks, S_NRM);
-                k_set_E<<<1, 1, 0, I.stream>>>(I.scal), ++I.nlaunch;
+                                                                    1.0 / (double)I.n_fluid, I.partials, I.red_stride,
+                                                                    I.ticket, L.nblocks), ++I.nlaunch;
             }
             OSCAR_LAUNCH_CHECK();
             OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
@@ -575,15 +505,15 @@ template <typename T> struct Impl {
             OSCAR_TRY(commit_alpha(I));
             P3<double> us;
             for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
+            double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
             if (I.g.dim == 3)
                 k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                     part(I, 0)), ++I.nlaunch;
+                                                                     I.partials, I.ticket, I.scal, I.ctl,
+                                                                     I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
             else
                 k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
-                                                                     part(I, 0)), ++I.nlaunch;
-            final_sum(I, 0, kRedBlocks, S_DUMAX, true);
-            double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
-            k_relax_control<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
+                                                                     I.partials, I.ticket, I.scal, I.ctl,
+                                                                     I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
             return 0;
         });
@@ -697,6 +627,14 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                                                                F.fluid, Lv.fluid), ++I.nlaunch;
     }
     OSCAR_LAUNCH_CHECK();
+    CLevels<T> P;
+    I.cta_smem = Impl<T>::cta_levels(I, P);
+    if (I.lev[I.lc0].g.ncell > 1024 || I.cta_smem > 200 * 1024) return OSCAR_E_INVALID_ARG;
+    cudaError_t e = I.g.dim == 3 ? cudaFuncSetAttribute(k_mg_coarse<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)I.cta_smem)
+                                 : cudaFuncSetAttribute(k_mg_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)I.cta_smem);
+    if (e != cudaSuccess) return OSCAR_E_CUDA;
     int rc = Impl<T>::interface_(I, I.alpha);
     I.nexec += I.nlaunch - l0;
     return rc;
@@ -757,10 +695,12 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)
                 k_cg_apply_dot<3, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, X::part(I, 0)), ++I.nlaunch;
+                                                                          (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
+                                                                          I.scal), ++I.nlaunch;
             else
                 k_cg_apply_dot<2, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, X::part(I, 0)), ++I.nlaunch;
+                                                                          (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
+                                                                          I.scal), ++I.nlaunch;
         } else if (kid == OSCAR_KID_MOMENTUM) {
             C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
             if (I.g.dim == 3)
@@ -866,9 +806,8 @@ template <typename T> int Solver<T>::field_from_device(Instance &I, int which, c
 }
 
 template <typename T> int Solver<T>::phase_volume(Instance &I, double *out) {
-    k_sum_field<T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const T *)I.alpha, I.g.V, I.partials), ++I.nlaunch,
-        ++I.nexec;
-    k_final<<<1, 1024, 0, I.stream>>>(I.partials, kRedBlocks, I.scal + S_VOL, 0), ++I.nlaunch, ++I.nexec;
+    k_sum_to<T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const T *)I.alpha, I.g.V, I.partials, I.ticket, I.scal,
+                                                 S_VOL), ++I.nlaunch, ++I.nexec;
     OSCAR_LAUNCH_CHECK();
     if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) != cudaSuccess)
         return OSCAR_E_CUDA;
