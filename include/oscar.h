@@ -180,6 +180,26 @@ int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *lau
  * three kernels as one launch. Waits for the stream. */
 int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms);
 
+/* Phase volume sum over fluid cells of alpha * cell_volume, computed without
+ * allocating any device memory. The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc, such as code running while
+ * a stream is being captured into a CUDA graph, or hosts that give the GPU a
+ * fixed memory budget and forbid later allocation.
+ *   alpha_dev   device double[ncell] (values in solid cells are ignored)
+ *   solid_dev   device uint8[ncell], 1 = solid
+ *   ncell       1 .. 16,777,216 cells; larger grids return OSCAR_E_INVALID_ARG
+ *   result_dev  device double[1] receiving the volume
+ *   stream      cudaStream_t of the call (NULL = default stream)
+ * Scratch: a 512 KiB static device array inside the library image, held by
+ * every GPU that loads the library until the process exits. The first call on
+ * a device looks up that array's device address (once per device, with that
+ * device current); make that first call before any stream capture. The
+ * result is not waited for. Every call shares the scratch, which keeps the
+ * last call's contents: calls that may overlap on the GPU (different streams,
+ * no ordering between them) race and must not be issued. */
+int oscar_phase_volume_noalloc(const double *alpha_dev, const uint8_t *solid_dev, long long ncell,
+                               double cell_volume, double *result_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

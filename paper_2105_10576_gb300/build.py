@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "liboscar_gb300.so")
-SOURCES = ["oscar_capi.cu", "oscar_fp64.cu", "oscar_mixed.cu"]
+SOURCES = ["oscar_capi.cu", "oscar_fp64.cu", "oscar_mixed.cu", "oscar_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(HERE, "..", "include")]

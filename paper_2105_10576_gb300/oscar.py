@@ -53,7 +53,8 @@ class oscar_stats_t(C.Structure):
 
 EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", "oscar_standard_step",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
-           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel"]
+           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel",
+           "oscar_phase_volume_noalloc"]
 KID_RBGS0, KID_CG_APPLY, KID_MOMENTUM, KID_TRANSPORT, KID_RESID0 = range(5)
 
 _lib = None
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.oscar_profile.argtypes = [H, C.c_int]
     lib.oscar_profile_read.argtypes = [H, C.c_int, dp, C.POINTER(C.c_longlong), C.c_int]
     lib.oscar_profile_kernel.argtypes = [H, C.c_int, C.c_int, dp]
+    lib.oscar_phase_volume_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_double, C.c_void_p,
+                                               C.c_void_p]
     _lib = lib
     return lib
 
@@ -203,3 +206,13 @@ class Oscar:
         st = oscar_stats_t()
         _check(self.lib.oscar_stats(self.h, C.byref(st)), "oscar_stats")
         return {name: getattr(st, name) for name, _ in oscar_stats_t._fields_}
+
+
+def oscar_phase_volume_noalloc(alpha_dev: int, solid_dev: int, ncell: int, cell_volume: float, result_dev: int,
+                               stream: int = 0) -> int:
+    """Phase volume of caller-owned device arrays with no device allocation
+    (for callers that cannot call cudaMalloc, e.g. during stream capture)."""
+    lib = load()
+    return _check(lib.oscar_phase_volume_noalloc(C.c_void_p(alpha_dev), C.c_void_p(solid_dev), ncell, cell_volume,
+                                                 C.c_void_p(result_dev), C.c_void_p(stream)),
+                  "oscar_phase_volume_noalloc")
