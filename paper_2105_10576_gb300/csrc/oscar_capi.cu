@@ -252,7 +252,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
     I.last_N = 1;
     I.mg_nu = 2;
-    I.mg_coarse_sweeps = 4;
+    I.mg_nu_c = 1;
+    I.mg_coarse_sweeps = 2;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
@@ -271,6 +272,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
         if (I.nlev - I.lc0 > 16) I.lc0 = I.nlev - 16;
         const char *enu = getenv("OSCAR_MG_NU");
         if (enu && atoi(enu) >= 1 && atoi(enu) <= 4) I.mg_nu = atoi(enu);
+        const char *enc = getenv("OSCAR_MG_NUC");
+        if (enc && atoi(enc) >= 1 && atoi(enc) <= 4) I.mg_nu_c = atoi(enc);
     }
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];

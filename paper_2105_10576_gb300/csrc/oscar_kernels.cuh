@@ -35,6 +35,11 @@ constexpr int BS = 256;
 constexpr int kCtaCells = 1024;      // levels at or below this size run in one CTA
 constexpr int kMaxCL = 16;
 
+// Programmatic dependent launch: every kernel is launched so that it may start
+// while its predecessor drains; it waits here, before touching any memory, for
+// the predecessor to complete and its writes to be visible.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int ftype(uint32_t info, int a, int s) { return (info >> (3 * (2 * a + s))) & 7; }
 
 struct GridD {
@@ -265,6 +270,7 @@ __device__ __forceinline__ void residual_control(double *scal, int *ctl, double 
 template <int DIM>
 __global__ void k_build_info(GridD g, const uint8_t *__restrict__ solid, uint32_t *__restrict__ info,
                              uint8_t *__restrict__ fluid) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     if (solid[c]) { info[c] = 0; fluid[c] = 0; return; }
@@ -288,6 +294,7 @@ __global__ void k_build_info(GridD g, const uint8_t *__restrict__ solid, uint32_
 
 template <typename T>
 __global__ void k_load_alpha(int n, const uint32_t *__restrict__ info, const double *__restrict__ src, T *__restrict__ dst) {
+    griddep_wait();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     dst[c] = (info[c] & INFO_FLUID) ? (T)src[c] : T(0);
@@ -295,12 +302,14 @@ __global__ void k_load_alpha(int n, const uint32_t *__restrict__ info, const dou
 
 template <typename S, typename D>
 __global__ void k_convert(int n, const S *__restrict__ src, D *__restrict__ dst) {
+    griddep_wait();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) dst[c] = (D)src[c];
 }
 
 template <typename T>
 __global__ void k_sum2(int n, const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out) {
+    griddep_wait();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) out[c] = a[c] + b[c];
 }
@@ -341,6 +350,7 @@ template <int DIM, typename T>
 __global__ void k_transport_low(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phi,
                                 C3<T> nf, T c_alpha, T alpha_in, T rV, T *__restrict__ aL, T *__restrict__ Pp,
                                 T *__restrict__ Pm) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -377,6 +387,7 @@ template <int DIM, typename T>
 __global__ void k_transport_ratio(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha,
                                   const T *__restrict__ aL, const T *__restrict__ Pp, const T *__restrict__ Pm, T rV,
                                   T *__restrict__ Rp, T *__restrict__ Rm) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -413,6 +424,7 @@ template <int DIM, typename T>
 __global__ void k_transport_update(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phi,
                                    C3<T> nf, T c_alpha, const T *__restrict__ aL, const T *__restrict__ Rp,
                                    const T *__restrict__ Rm, T rV, T *__restrict__ alpha_new) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -445,6 +457,7 @@ __global__ void k_transport_update(GridD g, const uint32_t *__restrict__ info, c
 // ---------------------------------------------------------------------------
 template <int DIM, typename T>
 __global__ void k_smooth(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ src, T *__restrict__ dst) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -479,6 +492,7 @@ __device__ __forceinline__ T gauss_grad(const GridD &g, const uint32_t *__restri
 template <int DIM, int A, typename T>
 __global__ void k_normals(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ as, T ct, T deltaN,
                           T *__restrict__ nfA) {
+    griddep_wait();
     FACE_IJK(g, A);
     int L, H;
     int t = decode_face<A>(g, info, i, j, k, L, H);
@@ -504,6 +518,7 @@ __global__ void k_normals(GridD g, const uint32_t *__restrict__ info, const T *_
 
 template <int DIM, typename T>
 __global__ void k_curvature(GridD g, const uint32_t *__restrict__ info, C3<T> nf, T *__restrict__ kappa) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     if (!(info[c] & INFO_FLUID)) { kappa[c] = T(0); return; }
@@ -523,6 +538,7 @@ template <typename T> __device__ __forceinline__ T mix(T al, T p1, T p2) { retur
 template <int DIM, typename T>
 __global__ void k_rA(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phic, Fluid<T> fl,
                      T dt, T *__restrict__ rA) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -557,6 +573,7 @@ template <int A, typename T>
 __global__ void k_face_coeffs(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ rA,
                               const T *__restrict__ kappa, const T *__restrict__ alpha, T sigma, int has_st,
                               T *__restrict__ cf, T *__restrict__ fst) {
+    griddep_wait();
     FACE_IJK(g, A);
     int L, H;
     int t = decode_face<A>(g, info, i, j, k, L, H);
@@ -575,6 +592,7 @@ __global__ void k_face_coeffs(GridD g, const uint32_t *__restrict__ info, const 
 // Gauss gradients of the velocity iterate: G[comp*3 + dir]
 template <int DIM, typename T>
 __global__ void k_vel_grad(GridD g, const uint32_t *__restrict__ info, C3<T> v, T vin0, P3<T> G0, P3<T> G1, P3<T> G2) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -608,6 +626,7 @@ template <int DIM, typename T>
 __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, C3<T> phic,
                              const T *__restrict__ alpha, const T *__restrict__ rA, Fluid<T> fl, T vin0, T dt,
                              C3<T> G0, C3<T> G1, C3<T> G2, P3<T> hbya) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -672,6 +691,7 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
 template <int A, typename T>
 __global__ void k_phistar(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ hbyaA,
                           const T *__restrict__ rA, const T *__restrict__ fst, T vinA, T *__restrict__ phis) {
+    griddep_wait();
     FACE_IJK(g, A);
     int L, H;
     int t = decode_face<A>(g, info, i, j, k, L, H);
@@ -686,6 +706,7 @@ __global__ void k_phistar(GridD g, const uint32_t *__restrict__ info, const T *_
 // b = -div(phi*), summed in T, stored in FP64
 template <int DIM, typename T>
 __global__ void k_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> phis, double *__restrict__ b) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     if (!(info[c] & INFO_FLUID)) { b[c] = 0.0; return; }
@@ -732,6 +753,7 @@ template <int DIM, typename T>
 __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
                           const double *__restrict__ b, double *__restrict__ scal, double inv_nf,
                           double *__restrict__ part, int stride, unsigned *__restrict__ ticket, int nb) {
+    griddep_wait();
     CELL_IJK(g);
     double qbar = scal[S_QSUM] * inv_nf;
     double res = 0.0, nrm = 0.0;
@@ -755,6 +777,7 @@ __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
 template <typename T>
 __global__ void k_sum_to(int n, const T *__restrict__ x, double scale, double *__restrict__ part,
                          unsigned *__restrict__ ticket, double *__restrict__ scal, int slot) {
+    griddep_wait();
     double acc = 0.0, dummy = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)x[c];
     if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) scal[slot] = acc * scale;
@@ -762,6 +785,7 @@ __global__ void k_sum_to(int n, const T *__restrict__ x, double scale, double *_
 
 template <typename T>
 __global__ void k_sum_field(int n, const T *__restrict__ x, double scale, double *__restrict__ part) {
+    griddep_wait();
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)x[c];
     acc = block_sum(acc);
@@ -773,6 +797,7 @@ __global__ void k_sum_field(int n, const T *__restrict__ x, double scale, double
 template <int A, typename T>
 __global__ void k_flux_correct(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ phis,
                                const T *__restrict__ cf, const double *__restrict__ q, T *__restrict__ phi) {
+    griddep_wait();
     FACE_IJK(g, A);
     int L, H;
     int t = decode_face<A>(g, info, i, j, k, L, H);
@@ -787,6 +812,7 @@ __global__ void k_flux_correct(GridD g, const uint32_t *__restrict__ info, const
 template <int DIM, typename T>
 __global__ void k_vel_correct(GridD g, const uint32_t *__restrict__ info, C3<T> hbya, const T *__restrict__ rA,
                               C3<T> fst, const double *__restrict__ q, P3<T> v) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     uint32_t inf = info[c];
@@ -824,6 +850,7 @@ template <int DIM, typename T>
 __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, P3<double> usum,
                               double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
                               int *__restrict__ ctl, int mode, double tol, double invU, cudaGraphConditionalHandle h) {
+    griddep_wait();
     double m = 0.0, dummy = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         if (!(info[c] & INFO_FLUID)) continue;
@@ -860,6 +887,7 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
                           const double *__restrict__ b, V *__restrict__ r, double *__restrict__ part, int stride,
                           unsigned *__restrict__ ticket, int nb, double *__restrict__ scal, int *__restrict__ ctl,
                           double rtol, int mode, cudaGraphConditionalHandle h) {
+    griddep_wait();
     CELL_IJK(g);
     double bb = 0.0, rr = 0.0;
     if (inside) {
@@ -885,6 +913,7 @@ template <int DIM, typename T, typename V>
 __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const V *__restrict__ p,
                                V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket, int nb,
                                double *__restrict__ scal) {
+    griddep_wait();
     CELL_IJK(g);
     double acc = 0.0, dummy = 0.0;
     if (inside) {
@@ -910,6 +939,7 @@ __global__ void k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V
                             const V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket,
                             double *__restrict__ scal, int *__restrict__ ctl, int maxit, int target_slot,
                             cudaGraphConditionalHandle h) {
+    griddep_wait();
     const V al = (V)scal[S_ALPHA];
     V accv = V(0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
@@ -937,6 +967,7 @@ __global__ void k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V
 template <typename V>
 __global__ void k_cg_dot_rz(int n, const V *__restrict__ x, const V *__restrict__ y, double *__restrict__ part,
                             unsigned *__restrict__ ticket, double *__restrict__ scal) {
+    griddep_wait();
     V accv = V(0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) accv += x[c] * y[c];
     double acc = (double)accv, dummy = 0.0;
@@ -950,6 +981,7 @@ __global__ void k_cg_dot_rz(int n, const V *__restrict__ x, const V *__restrict_
 // p = z + beta p
 template <typename V>
 __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__restrict__ z, V *__restrict__ p) {
+    griddep_wait();
     const V be = (V)scal[S_BETA];
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
 }
@@ -957,6 +989,7 @@ __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__
 // outer defect correction: q += e
 template <typename V>
 __global__ void k_cg_correct(int n, const V *__restrict__ e, double *__restrict__ q) {
+    griddep_wait();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) q[c] += (double)e[c];
 }
 
@@ -987,6 +1020,7 @@ __device__ __forceinline__ M mg_offdiag(const GridD &g, MG3<M> cc, const M *__re
 template <int DIM, typename M>
 __global__ void k_mg_rbgs(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, const M *__restrict__ diag,
                           M *__restrict__ x, const M *__restrict__ b, int colour) {
+    griddep_wait();
     const int ti = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -1003,6 +1037,7 @@ template <int DIM, typename M>
 __global__ void k_mg_resid_restrict(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
                                     MG3<M> cc, const M *__restrict__ diag, const M *__restrict__ x,
                                     const M *__restrict__ b, M *__restrict__ bc, M *__restrict__ xc) {
+    griddep_wait();
     CELL_IJK(gc);
     if (!inside) return;
     M acc = M(0);
@@ -1028,6 +1063,7 @@ __global__ void k_mg_resid_restrict(GridD gf, GridD gc, int rx, int ry, int rz, 
 template <typename M>
 __global__ void k_mg_prolong(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
                              const M *__restrict__ xc, M *__restrict__ x) {
+    griddep_wait();
     CELL_IJK(gf);
     if (!inside) return;
     if (!fluid[c]) return;
@@ -1036,6 +1072,7 @@ __global__ void k_mg_prolong(GridD gf, GridD gc, int rx, int ry, int rz, const u
 
 static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ ff,
                                           uint8_t *__restrict__ fc) {
+    griddep_wait();
     CELL_IJK(gc);
     if (!inside) return;
     uint8_t any = 0;
@@ -1053,6 +1090,7 @@ static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, in
 template <int A, typename M>
 __global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, const M *__restrict__ cfine,
                                   M *__restrict__ ccoarse) {
+    griddep_wait();
     FACE_IJK(gc, A);
     int rr[3] = {rx, ry, rz};
     int nfn[3] = {gf.nx, gf.ny, gf.nz};
@@ -1077,6 +1115,7 @@ __global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, co
 
 template <int DIM, typename M>
 __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, M *__restrict__ diag) {
+    griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
     if (!fluid[c]) { diag[c] = M(0); return; }
@@ -1097,10 +1136,10 @@ template <typename M> struct CLevel {
     const M *diag;
     const uint8_t *fluid;
     int r[3];          // ratios to the next level
-    int ox, ob, od, oc[3], ofl;   // shared-memory offsets (bytes)
+    int ox, ob, od, oc[3], ofl, opk;   // shared-memory offsets (bytes); opk: packed i | j<<10 | k<<20
 };
 template <typename M> struct CLevels {
-    int n, nu, coarse_sweeps;
+    int n, nu, nu_top, coarse_sweeps;
     const M *b_top;    // global b of the top level
     M *x_top;          // global x of the top level
     CLevel<M> L[kMaxCL];
@@ -1116,7 +1155,8 @@ __device__ __forceinline__ void cta_sweep(const CLevel<M> &L, unsigned char *sm,
     for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
     int cell = threadIdx.x;
     if (cell < g.ncell) {
-        int i = cell % g.nx, r = cell / g.nx, j = r % g.ny, k = r / g.ny;
+        int pk = ((const int *)(sm + L.opk))[cell];
+        int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
         if (((i + j + k) & 1) == colour && fl[cell] && d[cell] > M(0))
             x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d[cell];
     }
@@ -1125,6 +1165,7 @@ __device__ __forceinline__ void cta_sweep(const CLevel<M> &L, unsigned char *sm,
 
 template <int DIM, typename M>
 __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char sm[];
     const int t = threadIdx.x;
     for (int l = 0; l < P.n; ++l) {
@@ -1134,6 +1175,8 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
         for (int a = 0; a < DIM; ++a)
             for (int q = t; q < nf[a]; q += blockDim.x) ((M *)(sm + L.oc[a]))[q] = L.c[a][q];
         if (t < g.ncell) {
+            int r = t / g.nx;
+            ((int *)(sm + L.opk))[t] = (t - r * g.nx) | ((r % g.ny) << 10) | ((r / g.ny) << 20);
             ((M *)(sm + L.od))[t] = L.diag[t];
             (sm + L.ofl)[t] = L.fluid[t];
             ((M *)(sm + L.ox))[t] = M(0);
@@ -1144,13 +1187,15 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
     for (int l = 0; l < P.n - 1; ++l) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
-        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, sm, 0); cta_sweep<DIM, M>(L, sm, 1); }
+        const int nu = l == 0 ? P.nu_top : P.nu;
+        for (int s = 0; s < nu; ++s) { cta_sweep<DIM, M>(L, sm, 0); cta_sweep<DIM, M>(L, sm, 1); }
         const M *x = (const M *)(sm + L.ox), *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
         const uint8_t *fl = sm + L.ofl;
         MG3<M> cc;
         for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
         if (t < C.g.ncell) {
-            int I = t % C.g.nx, rr = t / C.g.nx, J = rr % C.g.ny, K = rr / C.g.ny;
+            int pk = ((const int *)(sm + C.opk))[t];
+            int I = pk & 1023, J = (pk >> 10) & 1023, K = pk >> 20;
             M acc = M(0);
             for (int oz = 0; oz < L.r[2]; ++oz) {
                 int kk = K * L.r[2] + oz;
@@ -1178,11 +1223,13 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
         if (t < L.g.ncell && (sm + L.ofl)[t]) {
-            int i = t % L.g.nx, r = t / L.g.nx, j = r % L.g.ny, k = r / L.g.ny;
+            int pk = ((const int *)(sm + L.opk))[t];
+            int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
             ((M *)(sm + L.ox))[t] += ((const M *)(sm + C.ox))[(i / L.r[0]) + C.g.nx * ((j / L.r[1]) + C.g.ny * (k / L.r[2]))];
         }
         __syncthreads();
-        for (int s = 0; s < P.nu; ++s) { cta_sweep<DIM, M>(L, sm, 1); cta_sweep<DIM, M>(L, sm, 0); }
+        const int nu = l == 0 ? P.nu_top : P.nu;
+        for (int s = 0; s < nu; ++s) { cta_sweep<DIM, M>(L, sm, 1); cta_sweep<DIM, M>(L, sm, 0); }
     }
     if (t < P.L[0].g.ncell) P.x_top[t] = ((const M *)(sm + P.L[0].ox))[t];
 }

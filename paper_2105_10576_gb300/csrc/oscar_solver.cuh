@@ -33,6 +33,24 @@ namespace oscar {
 
 inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
 
+// Kernel launch with programmatic stream serialization: the next kernel's
+// launch overlaps the tail of this one (each kernel waits in griddep_wait()).
+template <typename... KArgs, typename... Args>
+inline void launchk(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 
 // ---------------------------------------------------------------------------
 // control kernels (one thread). The other loop decisions are taken by the
@@ -40,12 +58,14 @@ inline int nblk(long long n) { return (int)((n + BS - 1) / BS); }
 // k_relax_accum).
 // ---------------------------------------------------------------------------
 static __global__ void k_inner_start(double *scal, int *ctl, cudaGraphConditionalHandle h) {
+    griddep_wait();
     scal[S_RZ0] = 0.0;
     ctl[C_IT] = 0;
     set_cond(ctl, h, true);
 }
 
-static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) { set_cond(ctl, h, ctl[C_N] > 0); }
+static __global__ void k_relax_init(int *ctl, cudaGraphConditionalHandle h) {
+    griddep_wait(); set_cond(ctl, h, ctl[C_N] > 0); }
 
 // ---------------------------------------------------------------------------
 // capture helpers
@@ -147,12 +167,12 @@ template <typename T> struct Impl {
         L3 L = launch3(I.g);
         T rV = (T)(dt / I.g.V);
         int ps = prof_begin(I, OSCAR_KID_TRANSPORT);
-        k_transport_low<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
+        launchk(k_transport_low<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
                                                                   (T)I.P.c_alpha, (T)I.P.alpha_inlet, rV, tp(I.aL),
                                                                   tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
-        k_transport_ratio<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp),
+        launchk(k_transport_ratio<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(I.alpha), tp(I.aL), tp(I.Pp),
                                                                     tp(I.Pm), rV, tp(I.Rp), tp(I.Rm)), ++I.nlaunch;
-        k_transport_update<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
+        launchk(k_transport_update<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
                                                                      (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
                                                                      tp(I.alpha_new)), ++I.nlaunch;
         prof_end(I, ps);
@@ -171,17 +191,17 @@ template <typename T> struct Impl {
         void *src = alpha;
         for (int pass = 0; pass < I.P.n_smooth; ++pass) {
             void *dst = (pass % 2 == 0) ? I.alpha_s : I.alpha_tmp;
-            k_smooth<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, tp(src), tp(dst)), ++I.nlaunch;
+            launchk(k_smooth<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(src), tp(dst)), ++I.nlaunch;
             src = dst;
         }
         const T *as = tp(src);
         T ct = (T)I.cos_theta, dn = (T)I.deltaN;
         L3 F0 = launch3_faces(I.g, 0), F1 = launch3_faces(I.g, 1), F2 = launch3_faces(I.g, 2);
-        k_normals<DIM, 0, T><<<F0.grid, F0.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
-        k_normals<DIM, 1, T><<<F1.grid, F1.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
+        launchk(k_normals<DIM, 0, T>, F0.grid, F0.block, 0, I.stream, g, I.info, as, ct, dn, tp(I.nf[0])), ++I.nlaunch;
+        launchk(k_normals<DIM, 1, T>, F1.grid, F1.block, 0, I.stream, g, I.info, as, ct, dn, tp(I.nf[1])), ++I.nlaunch;
         if (DIM == 3)
-            k_normals<DIM, 2, T><<<F2.grid, F2.block, 0, I.stream>>>(g, I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
-        k_curvature<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
+            launchk(k_normals<DIM, 2, T>, F2.grid, F2.block, 0, I.stream, g, I.info, as, ct, dn, tp(I.nf[2])), ++I.nlaunch;
+        launchk(k_curvature<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.nf), tp(I.kappa)), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
@@ -203,18 +223,18 @@ template <typename T> struct Impl {
                 for (int a = 0; a < DIM; ++a) {
                     L3 FL = launch3_faces(L.g, a);
                     if (a == 0)
-                        k_mg_coarse_coeff<0, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                        launchk(k_mg_coarse_coeff<0, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
                                                                                   (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
                     else if (a == 1)
-                        k_mg_coarse_coeff<1, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                        launchk(k_mg_coarse_coeff<1, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
                                                                                   (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
                     else
-                        k_mg_coarse_coeff<2, M><<<FL.grid, FL.block, 0, I.stream>>>(gf, g, F.r[0], F.r[1], F.r[2],
+                        launchk(k_mg_coarse_coeff<2, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
                                                                                   (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
                 }
             }
             L3 LL = launch3(L.g);
-            k_mg_diag<DIM, M><<<LL.grid, LL.block, 0, I.stream>>>(g, L.fluid, mg3(L), (M *)L.diag), ++I.nlaunch;
+            launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag), ++I.nlaunch;
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -223,7 +243,8 @@ template <typename T> struct Impl {
     // levels lc0.. of the single-CTA coarse kernel with their shared-memory layout
     static size_t cta_levels(Instance &I, CLevels<M> &P) {
         P.n = I.nlev - I.lc0;
-        P.nu = I.mg_nu;
+        P.nu = I.mg_nu_c;
+        P.nu_top = I.lc0 == 0 ? I.mg_nu : I.mg_nu_c;
         P.coarse_sweeps = I.mg_coarse_sweeps;
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
@@ -241,6 +262,7 @@ template <typename T> struct Impl {
             C.od = take(n * sizeof(M));
             for (int a = 0; a < 3; ++a) C.oc[a] = take((size_t)L.g.nf[a] * sizeof(M));
             C.ofl = take(n);
+            C.opk = take(n * sizeof(int));
         }
         return off;
     }
@@ -255,7 +277,7 @@ template <typename T> struct Impl {
         GridD g = to_dev(L.g);
         L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
         int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
-        k_mg_rbgs<DIM, M><<<LL.grid, LL.block, 0, I.stream>>>(g, L.fluid, mg3(L), (const M *)L.diag, x, b, colour),
+        launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (const M *)L.diag, x, b, colour),
             ++I.nlaunch;
         prof_end(I, ps);
     }
@@ -266,15 +288,15 @@ template <typename T> struct Impl {
     template <int DIM>
     static int vcycle_d(Instance &I, V *r, V *z) {
         if (cudaMemsetAsync(z, 0, (size_t)I.g.ncell * sizeof(V), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
-        int nu = I.mg_nu;
         for (int l = 0; l < I.lc0; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
+            int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
             for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0, x, b); smooth_level<DIM>(I, l, 1, x, b); }
             GridD g = to_dev(L.g), gc = to_dev(C.g);
             L3 LC = launch3(C.g);
             int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-            k_mg_resid_restrict<DIM, M><<<LC.grid, LC.block, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
+            launchk(k_mg_resid_restrict<DIM, M>, LC.grid, LC.block, 0, I.stream, g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
                                                                            mg3(L), (const M *)L.diag, x, b,
                                                                            lb(I, l + 1, r), lx(I, l + 1, z)), ++I.nlaunch;
             prof_end(I, ps);
@@ -283,13 +305,14 @@ template <typename T> struct Impl {
         cta_levels(I, P);
         P.b_top = lb(I, I.lc0, r);
         P.x_top = lx(I, I.lc0, z);
-        k_mg_coarse<DIM, M><<<1, 1024, I.cta_smem, I.stream>>>(P), ++I.nlaunch;
+        launchk(k_mg_coarse<DIM, M>, 1, 1024, I.cta_smem, I.stream, P), ++I.nlaunch;
         for (int l = I.lc0 - 1; l >= 0; --l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
+            int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
             GridD g = to_dev(L.g), gc = to_dev(C.g);
             L3 LL = launch3(L.g);
-            k_mg_prolong<M><<<LL.grid, LL.block, 0, I.stream>>>(g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
+            launchk(k_mg_prolong<M>, LL.grid, LL.block, 0, I.stream, g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
                                                                 (const M *)lx(I, l + 1, z), x), ++I.nlaunch;
             for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1, x, b); smooth_level<DIM>(I, l, 0, x, b); }
         }
@@ -303,7 +326,7 @@ template <typename T> struct Impl {
     static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h) {
         GridD g = to_dev(I.g);
         L3 L = launch3(I.g);
-        k_cg_init<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, I.partials,
+        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, I.partials,
                                                                I.red_stride, I.ticket, L.nblocks, I.scal, I.ctl,
                                                                I.P.cg_rtol, mode, h), ++I.nlaunch;
     }
@@ -317,13 +340,13 @@ template <typename T> struct Impl {
         V *r = (V *)I.cg_r, *z = (V *)I.cg_z, *p = (V *)I.cg_p, *Ap = (V *)I.cg_Ap;
         long long n0 = I.nlaunch;
         OSCAR_TRY(vcycle_d<DIM>(I, r, z));
-        k_cg_dot_rz<V><<<kRedBlocks, BS, 0, I.stream>>>(n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
-        k_cg_pupdate<V><<<kRedBlocks, BS, 0, I.stream>>>(n, I.scal, z, p), ++I.nlaunch;
+        launchk(k_cg_dot_rz<V>, kRedBlocks, BS, 0, I.stream, n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
+        launchk(k_cg_pupdate<V>, kRedBlocks, BS, 0, I.stream, n, I.scal, z, p), ++I.nlaunch;
         int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-        k_cg_apply_dot<DIM, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.lev[0].c), p, Ap, I.partials,
+        launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap, I.partials,
                                                                     I.ticket, L.nblocks, I.scal), ++I.nlaunch;
         prof_end(I, ps);
-        k_cg_update<V><<<kRedBlocks, BS, 0, I.stream>>>(n, x, r, p, Ap, I.partials, I.ticket, I.scal, I.ctl,
+        launchk(k_cg_update<V>, kRedBlocks, BS, 0, I.stream, n, x, r, p, Ap, I.partials, I.ticket, I.scal, I.ctl,
                                                         I.P.cg_maxit, target_slot, h), ++I.nlaunch;
         if (I.capturing) {
             I.n_cg_body = I.nlaunch - n0;
@@ -355,9 +378,9 @@ template <typename T> struct Impl {
                 return OSCAR_E_CUDA;
             cudaGraphConditionalHandle hi;
             OSCAR_TRY(cond_handle(I, &hi));
-            k_inner_start<<<1, 1, 0, I.stream>>>(I.scal, I.ctl, hi), ++I.nlaunch;
+            launchk(k_inner_start, 1, 1, 0, I.stream, I.scal, I.ctl, hi), ++I.nlaunch;
             OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi); }));
-            k_cg_correct<V><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
+            launchk(k_cg_correct<V>, kRedBlocks, BS, 0, I.stream, I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
             residual64<DIM>(I, q, b, 2, ho);
             if (I.capturing) I.n_outer_body = (I.nlaunch - n0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
             OSCAR_LAUNCH_CHECK();
@@ -374,53 +397,53 @@ template <typename T> struct Impl {
         L3 F[3] = {launch3_faces(I.g, 0), launch3_faces(I.g, 1), launch3_faces(I.g, 2)};
         Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
         const T *al = tp(I.alpha_new);
-        k_rA<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
+        launchk(k_rA<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, al, c3(I.phic), fl, (T)dt, tp(I.rA)), ++I.nlaunch;
         void **cf = I.lev[0].c;
         T sig = (T)I.P.sigma;
         int st = has_st ? 1 : 0;
-        k_face_coeffs<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+        launchk(k_face_coeffs<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
                                                                     tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
-        k_face_coeffs<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+        launchk(k_face_coeffs<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
                                                                     tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
         if (DIM == 3)
-            k_face_coeffs<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
+            launchk(k_face_coeffs<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
                                                                         tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         OSCAR_TRY(mg_coeffs_d<DIM>(I));
         P3<T> Gp0 = p3(&I.G[0]), Gp1 = p3(&I.G[3]), Gp2 = p3(&I.G[6]);
         C3<T> Gc0 = c3(&I.G[0]), Gc1 = c3(&I.G[3]), Gc2 = c3(&I.G[6]);
         for (int corr = 0; corr < I.P.n_piso; ++corr) {
-            k_vel_grad<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
+            launchk(k_vel_grad<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
             int ps = prof_begin(I, OSCAR_KID_MOMENTUM);
-            k_momentum_H<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(v), c3(I.vold), c3(I.phic), al,
+            launchk(k_momentum_H<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(v), c3(I.vold), c3(I.phic), al,
                                                                    tp(I.rA), fl, (T)vin0, (T)dt, Gc0, Gc1, Gc2,
                                                                    p3(I.hbya)), ++I.nlaunch;
             prof_end(I, ps);
-            k_phistar<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.hbya[0]), tp(I.rA), tp(I.fst[0]),
+            launchk(k_phistar<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.hbya[0]), tp(I.rA), tp(I.fst[0]),
                                                                     (T)vin0, tp(I.phis[0])), ++I.nlaunch;
-            k_phistar<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.hbya[1]), tp(I.rA), tp(I.fst[1]),
+            launchk(k_phistar<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.hbya[1]), tp(I.rA), tp(I.fst[1]),
                                                                     T(0), tp(I.phis[1])), ++I.nlaunch;
             if (DIM == 3)
-                k_phistar<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.hbya[2]), tp(I.rA),
+                launchk(k_phistar<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.hbya[2]), tp(I.rA),
                                                                         tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
-            k_rhs<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
+            launchk(k_rhs<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
             if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
-                k_sum_to<double><<<kRedBlocks, BS, 0, I.stream>>>(g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
+                launchk(k_sum_to<double>, kRedBlocks, BS, 0, I.stream, g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
                                                                   S_QSUM), ++I.nlaunch;
-                k_normres<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(cf), q, I.cg_b, I.scal,
+                launchk(k_normres<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(cf), q, I.cg_b, I.scal,
                                                                     1.0 / (double)I.n_fluid, I.partials, I.red_stride,
                                                                     I.ticket, L.nblocks), ++I.nlaunch;
             }
             OSCAR_LAUNCH_CHECK();
             OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
-            k_flux_correct<0, T><<<F[0].grid, F[0].block, 0, I.stream>>>(g, I.info, tp(I.phis[0]), tp(cf[0]), q,
+            launchk(k_flux_correct<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.phis[0]), tp(cf[0]), q,
                                                                          tp(phi[0])), ++I.nlaunch;
-            k_flux_correct<1, T><<<F[1].grid, F[1].block, 0, I.stream>>>(g, I.info, tp(I.phis[1]), tp(cf[1]), q,
+            launchk(k_flux_correct<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.phis[1]), tp(cf[1]), q,
                                                                          tp(phi[1])), ++I.nlaunch;
             if (DIM == 3)
-                k_flux_correct<2, T><<<F[2].grid, F[2].block, 0, I.stream>>>(g, I.info, tp(I.phis[2]), tp(cf[2]), q,
+                launchk(k_flux_correct<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.phis[2]), tp(cf[2]), q,
                                                                              tp(phi[2])), ++I.nlaunch;
-            k_vel_correct<DIM, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q,
+            launchk(k_vel_correct<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q,
                                                                     p3(v)), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
         }
@@ -440,7 +463,7 @@ template <typename T> struct Impl {
     }
     static int sum_faces(Instance &I, void *const *a, void *const *b, void *const *out) {
         for (int d = 0; d < I.g.dim; ++d)
-            k_sum2<T><<<nblk(I.g.nf[d]), BS, 0, I.stream>>>(I.g.nf[d], tp(a[d]), tp(b[d]), tp(out[d])), ++I.nlaunch;
+            launchk(k_sum2<T>, nblk(I.g.nf[d]), BS, 0, I.stream, I.g.nf[d], tp(a[d]), tp(b[d]), tp(out[d])), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
@@ -487,7 +510,7 @@ template <typename T> struct Impl {
                 return OSCAR_E_CUDA;
         cudaGraphConditionalHandle h;
         OSCAR_TRY(cond_handle(I, &h));
-        k_relax_init<<<1, 1, 0, I.stream>>>(I.ctl, h), ++I.nlaunch;
+        launchk(k_relax_init, 1, 1, 0, I.stream, I.ctl, h), ++I.nlaunch;
         *n_pre = I.nlaunch - s0;
         long long b0 = I.nlaunch, cg0 = I.cg_bodies_captured;
         long long ob0 = I.cg_bodies_captured;
@@ -507,11 +530,11 @@ template <typename T> struct Impl {
             for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
             double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
             if (I.g.dim == 3)
-                k_relax_accum<3, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                launchk(k_relax_accum<3, T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
                                                                      I.partials, I.ticket, I.scal, I.ctl,
                                                                      I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
             else
-                k_relax_accum<2, T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
+                launchk(k_relax_accum<2, T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, I.info, c3(I.u_cr), c3(I.vold), us,
                                                                      I.partials, I.ticket, I.scal, I.ctl,
                                                                      I.P.conv_mode, I.P.conv_tol, invU, h), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
@@ -617,13 +640,13 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
     GridD g = to_dev(I.g);
     L3 L = launch3(I.g);
     long long l0 = I.nlaunch;
-    if (I.g.dim == 3) k_build_info<3><<<L.grid, L.block, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    else k_build_info<2><<<L.grid, L.block, 0, I.stream>>>(g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
-    k_load_alpha<T><<<nblk(g.ncell), BS, 0, I.stream>>>(g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
+    if (I.g.dim == 3) launchk(k_build_info<3>, L.grid, L.block, 0, I.stream, g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    else launchk(k_build_info<2>, L.grid, L.block, 0, I.stream, g, solid_dev, I.info, I.lev[0].fluid), ++I.nlaunch;
+    launchk(k_load_alpha<T>, nblk(g.ncell), BS, 0, I.stream, g.ncell, I.info, alpha0_dev, (T *)I.alpha), ++I.nlaunch;
     for (int l = 1; l < I.nlev; ++l) {
         Level &F = I.lev[l - 1], &Lv = I.lev[l];
         L3 LC = launch3(Lv.g);
-        k_mg_fluid_coarsen<<<LC.grid, LC.block, 0, I.stream>>>(to_dev(F.g), to_dev(Lv.g), F.r[0], F.r[1], F.r[2],
+        launchk(k_mg_fluid_coarsen, LC.grid, LC.block, 0, I.stream, to_dev(F.g), to_dev(Lv.g), F.r[0], F.r[1], F.r[2],
                                                                F.fluid, Lv.fluid), ++I.nlaunch;
     }
     OSCAR_LAUNCH_CHECK();
@@ -684,32 +707,32 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
                 Level &C = I.lev[1];
                 L3 LC = launch3(C.g);
                 if (I.g.dim == 3)
-                    k_mg_resid_restrict<3, T><<<LC.grid, LC.block, 0, I.stream>>>(
+                    launchk(k_mg_resid_restrict<3, T>, LC.grid, LC.block, 0, I.stream, 
                         g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
                         (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
                 else
-                    k_mg_resid_restrict<2, T><<<LC.grid, LC.block, 0, I.stream>>>(
+                    launchk(k_mg_resid_restrict<2, T>, LC.grid, LC.block, 0, I.stream, 
                         g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
                         (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
             }
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)
-                k_cg_apply_dot<3, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                launchk(k_cg_apply_dot<3, T, V>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
                                                                           (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
                                                                           I.scal), ++I.nlaunch;
             else
-                k_cg_apply_dot<2, T, V><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                launchk(k_cg_apply_dot<2, T, V>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
                                                                           (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
                                                                           I.scal), ++I.nlaunch;
         } else if (kid == OSCAR_KID_MOMENTUM) {
             C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
             if (I.g.dim == 3)
-                k_momentum_H<3, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold),
+                launchk(k_momentum_H<3, T>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.u_cr), X::c3(I.vold),
                                                                      X::c3(I.phic), (const T *)I.alpha_new,
                                                                      (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
                                                                      X::p3(I.hbya)), ++I.nlaunch;
             else
-                k_momentum_H<2, T><<<L.grid, L.block, 0, I.stream>>>(g, I.info, X::c3(I.u_cr), X::c3(I.vold),
+                launchk(k_momentum_H<2, T>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.u_cr), X::c3(I.vold),
                                                                      X::c3(I.phic), (const T *)I.alpha_new,
                                                                      (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
                                                                      X::p3(I.hbya)), ++I.nlaunch;
@@ -735,11 +758,13 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
 template <typename T>
 __global__ void k_report_u(int n, const T *__restrict__ uvd, const double *__restrict__ usum, double invN,
                            double *__restrict__ out) {
+    griddep_wait();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) out[c] = (double)uvd[c] + usum[c] * invN;
 }
 static __global__ void k_add_pd(int n, const double *__restrict__ a, const double *__restrict__ b,
                                 double *__restrict__ out) {
+    griddep_wait();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c < n) out[c] = a[c] + b[c];
 }
@@ -748,14 +773,14 @@ template <typename T> int Solver<T>::field_to_device(Instance &I, int which, dou
     int nc = I.g.ncell;
     cudaStream_t s = I.stream;
     auto cvt = [&](const void *src, size_t len) {
-        k_convert<T, double><<<nblk(len), BS, 0, s>>>((int)len, (const T *)src, dst), ++I.nlaunch, ++I.nexec;
+        launchk(k_convert<T, double>, nblk(len), BS, 0, s, (int)len, (const T *)src, dst), ++I.nlaunch, ++I.nexec;
     };
     if (which == OSCAR_FIELD_ALPHA) cvt(I.alpha, nc);
-    else if (which == OSCAR_FIELD_P) k_add_pd<<<nblk(nc), BS, 0, s>>>(nc, I.p_vd, I.p_cr, dst), ++I.nlaunch, ++I.nexec;
+    else if (which == OSCAR_FIELD_P) launchk(k_add_pd, nblk(nc), BS, 0, s, nc, I.p_vd, I.p_cr, dst), ++I.nlaunch, ++I.nexec;
     else if (which >= 2 && which <= 4) {
         int a = which - 2;
         if (a >= I.g.dim) cudaMemsetAsync(dst, 0, n * sizeof(double), s);
-        else k_report_u<T><<<nblk(nc), BS, 0, s>>>(nc, (const T *)I.u_vd[a], I.u_sum[a], 1.0 / (double)I.last_N, dst),
+        else launchk(k_report_u<T>, nblk(nc), BS, 0, s, nc, (const T *)I.u_vd[a], I.u_sum[a], 1.0 / (double)I.last_N, dst),
                  ++I.nlaunch, ++I.nexec;
     } else if (which >= 5 && which <= 10) {
         int a = (which - 5) % 3;
@@ -779,10 +804,10 @@ template <typename T> int Solver<T>::field_from_device(Instance &I, int which, c
     int nc = I.g.ncell;
     cudaStream_t s = I.stream;
     auto cvt = [&](void *dst, size_t len) {
-        k_convert<double, T><<<nblk(len), BS, 0, s>>>((int)len, src, (T *)dst), ++I.nlaunch, ++I.nexec;
+        launchk(k_convert<double, T>, nblk(len), BS, 0, s, (int)len, src, (T *)dst), ++I.nlaunch, ++I.nexec;
     };
     if (which == OSCAR_FIELD_ALPHA) {
-        k_load_alpha<T><<<nblk(nc), BS, 0, s>>>(nc, I.info, src, (T *)I.alpha), ++I.nlaunch, ++I.nexec;
+        launchk(k_load_alpha<T>, nblk(nc), BS, 0, s, nc, I.info, src, (T *)I.alpha), ++I.nlaunch, ++I.nexec;
         OSCAR_LAUNCH_CHECK();
         long long l0 = I.nlaunch;
         int rc = Impl<T>::interface_(I, I.alpha);
@@ -806,7 +831,7 @@ template <typename T> int Solver<T>::field_from_device(Instance &I, int which, c
 }
 
 template <typename T> int Solver<T>::phase_volume(Instance &I, double *out) {
-    k_sum_to<T><<<kRedBlocks, BS, 0, I.stream>>>(I.g.ncell, (const T *)I.alpha, I.g.V, I.partials, I.ticket, I.scal,
+    launchk(k_sum_to<T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, (const T *)I.alpha, I.g.V, I.partials, I.ticket, I.scal,
                                                  S_VOL), ++I.nlaunch, ++I.nexec;
     OSCAR_LAUNCH_CHECK();
     if (cudaMemcpyAsync(I.scal_host, I.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, I.stream) != cudaSuccess)
