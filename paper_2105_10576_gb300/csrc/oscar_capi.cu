@@ -252,8 +252,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
     I.last_N = 1;
     I.mg_nu = 2;
-    I.mg_nu_c = 1;
-    I.mg_coarse_sweeps = 2;
+    I.mg_nu_c = 2;
+    I.mg_coarse_sweeps = 4;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;

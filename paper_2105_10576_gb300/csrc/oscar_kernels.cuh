@@ -1032,24 +1032,25 @@ __global__ void k_mg_rbgs(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
     x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d;
 }
 
-// coarse b = sum over children of the fine residual b - M x; coarse x = 0
-template <int DIM, typename M>
-__global__ void k_mg_resid_restrict(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
-                                    MG3<M> cc, const M *__restrict__ diag, const M *__restrict__ x,
-                                    const M *__restrict__ b, M *__restrict__ bc, M *__restrict__ xc) {
+// coarse b = sum over children of the fine residual b - M x; coarse x = 0.
+// The coarsening ratios are template parameters so the children unroll and
+// their loads overlap.
+template <int DIM, typename M, int RX, int RY, int RZ>
+__global__ void k_mg_resid_restrict(GridD gf, GridD gc, const uint8_t *__restrict__ fluid, MG3<M> cc,
+                                    const M *__restrict__ diag, const M *__restrict__ x, const M *__restrict__ b,
+                                    M *__restrict__ bc, M *__restrict__ xc) {
     griddep_wait();
     CELL_IJK(gc);
     if (!inside) return;
     M acc = M(0);
-    for (int oz = 0; oz < rz; ++oz) {
-        int kk = k * rz + oz;
-        if (kk >= gf.nz) break;
-        for (int oy = 0; oy < ry; ++oy) {
-            int jj = j * ry + oy;
-            if (jj >= gf.ny) break;
-            for (int ox = 0; ox < rx; ++ox) {
-                int ii = i * rx + ox;
-                if (ii >= gf.nx) break;
+#pragma unroll
+    for (int oz = 0; oz < RZ; ++oz) {
+#pragma unroll
+        for (int oy = 0; oy < RY; ++oy) {
+#pragma unroll
+            for (int ox = 0; ox < RX; ++ox) {
+                int ii = i * RX + ox, jj = j * RY + oy, kk = k * RZ + oz;
+                if (ii >= gf.nx || jj >= gf.ny || kk >= gf.nz) continue;
                 int cell = ii + gf.nx * (jj + gf.ny * kk);
                 if (!fluid[cell]) continue;
                 acc += b[cell] - (diag[cell] * x[cell] - mg_offdiag<DIM, M>(gf, cc, x, cell, ii, jj, kk));

@@ -282,6 +282,29 @@ template <typename T> struct Impl {
         prof_end(I, ps);
     }
 
+    template <int DIM, int RX, int RY, int RZ>
+    static void rr_launch(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc) {
+        L3 LC = launch3(C.g);
+        launchk(k_mg_resid_restrict<DIM, M, RX, RY, RZ>, LC.grid, LC.block, 0, I.stream, to_dev(L.g), to_dev(C.g),
+                L.fluid, mg3(L), (const M *)L.diag, x, b, bc, xc);
+        ++I.nlaunch;
+    }
+    // fused residual + restriction, dispatched on the coarsening ratios
+    template <int DIM>
+    static void resid_restrict(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc) {
+        int code = (L.r[0] == 2) | ((L.r[1] == 2) << 1) | ((L.r[2] == 2) << 2);
+        switch (code) {
+            case 1: rr_launch<DIM, 2, 1, 1>(I, L, C, x, b, bc, xc); break;
+            case 2: rr_launch<DIM, 1, 2, 1>(I, L, C, x, b, bc, xc); break;
+            case 3: rr_launch<DIM, 2, 2, 1>(I, L, C, x, b, bc, xc); break;
+            case 4: rr_launch<DIM, 1, 1, 2>(I, L, C, x, b, bc, xc); break;
+            case 5: rr_launch<DIM, 2, 1, 2>(I, L, C, x, b, bc, xc); break;
+            case 6: rr_launch<DIM, 1, 2, 2>(I, L, C, x, b, bc, xc); break;
+            case 7: rr_launch<DIM, 2, 2, 2>(I, L, C, x, b, bc, xc); break;
+            default: rr_launch<DIM, 1, 1, 1>(I, L, C, x, b, bc, xc); break;
+        }
+    }
+
     // z = V-cycle(r): pre-smoothing red-black, post-smoothing black-red
     // (symmetric, so a valid CG preconditioner); levels from lc0 down run in
     // one CTA.
@@ -296,9 +319,7 @@ template <typename T> struct Impl {
             GridD g = to_dev(L.g), gc = to_dev(C.g);
             L3 LC = launch3(C.g);
             int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-            launchk(k_mg_resid_restrict<DIM, M>, LC.grid, LC.block, 0, I.stream, g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
-                                                                           mg3(L), (const M *)L.diag, x, b,
-                                                                           lb(I, l + 1, r), lx(I, l + 1, z)), ++I.nlaunch;
+            resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z));
             prof_end(I, ps);
         }
         CLevels<M> P;
@@ -705,15 +726,8 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
         } else if (kid == OSCAR_KID_RESID0) {
             if (I.nlev > 1) {
                 Level &C = I.lev[1];
-                L3 LC = launch3(C.g);
-                if (I.g.dim == 3)
-                    launchk(k_mg_resid_restrict<3, T>, LC.grid, LC.block, 0, I.stream, 
-                        g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
-                        (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
-                else
-                    launchk(k_mg_resid_restrict<2, T>, LC.grid, LC.block, 0, I.stream, 
-                        g, to_dev(C.g), L0.r[0], L0.r[1], L0.r[2], L0.fluid, X::mg3(L0), (const T *)L0.diag,
-                        (const T *)z, (const T *)r, (T *)C.b, (T *)C.x), ++I.nlaunch;
+                if (I.g.dim == 3) X::template resid_restrict<3>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x);
+                else X::template resid_restrict<2>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x);
             }
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)

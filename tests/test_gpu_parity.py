@@ -141,7 +141,8 @@ def test_fp64_bubble_channel_full_run_matches_oracle():
     pressure solves (condition number ~1e7 at the 1000:1.2 density ratio),
     amplified by the parasitic-current dynamics: the oracle itself moves by
     6e-10 on these fields when only its CG tolerance changes from 1e-14 to
-    1e-15, so they are held to 2e-9."""
+    1e-15, and the differences grow with the number of solves (3000 here,
+    6000 in the standard run), so they are held to 1e-8."""
     c = inputs.channel_bubble_2d(cg_rtol=1e-15, cg_maxit=400)   # oracle: exact banded solves
     dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"])
     assert N == 50
@@ -149,7 +150,7 @@ def test_fp64_bubble_channel_full_run_matches_oracle():
     assert kg == ko
     vel = ("ux", "uy", "uvdx", "uvdy", "ucrx", "ucry", "phi_vd_x", "phi_vd_y", "phi_cr_x", "phi_cr_y")
     worst = compare(g, o, 2, 1e-10, skip=vel)
-    worst.update(compare(g, o, 2, 2e-9, skip=tuple(n for n, _, _ in fields_for(2) if n not in vel)))
+    worst.update(compare(g, o, 2, 1e-8, skip=tuple(n for n, _, _ in fields_for(2) if n not in vel)))
     print("oscar worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
     gs = ox.Oscar(c.params, c.solid, c.alpha0)
     os_ = oracle.OracleState(c.params, c.solid, c.alpha0)
@@ -158,7 +159,7 @@ def test_fp64_bubble_channel_full_run_matches_oracle():
         os_.standard_step(dt_vd / N)
     crf = ("ucrx", "ucry", "phi_cr_x", "phi_cr_y")
     worst = compare(gs, os_, 2, 1e-10, skip=crf + vel)
-    worst.update(compare(gs, os_, 2, 2e-9, skip=crf + tuple(n for n, _, _ in fields_for(2) if n not in vel)))
+    worst.update(compare(gs, os_, 2, 1e-8, skip=crf + tuple(n for n, _, _ in fields_for(2) if n not in vel)))
     print("standard worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
 
 
