@@ -79,6 +79,30 @@ def algorithmic_bytes(kid: int, c, es: int) -> float:
     raise ValueError(kid)
 
 
+def recorded_traffic(kid: int):
+    """DRAM bytes per launch of kernel class kid from the committed ncu summary,
+    or None when there is none or the kernel source changed since the capture."""
+    import hashlib
+    files = {0: "k_mg_rbgs_constriction_3d.md"}
+    if kid not in files:
+        return None
+    path = os.path.join(ROOT, "profiles", files[kid])
+    src = os.path.join(ROOT, "paper_2105_10576_gb300", "csrc", "oscar_kernels.cuh")
+    try:
+        txt = open(path).read()
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    rec = {}
+    for line in txt.splitlines():
+        if ":" in line and line.split(":")[0] in ("kernel_source_sha1", "traffic_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            rec[k] = v.split()[0]
+    if rec.get("kernel_source_sha1") != sha or "traffic_bytes_per_launch" not in rec:
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
 KID_NAMES = {0: "k_mg_rbgs (finest level, half sweep)", 1: "k_cg_apply_dot", 2: "k_momentum_H",
              3: "k_transport_{low,ratio,update}", 4: "k_mg_residual (finest level)"}
 
@@ -306,7 +330,8 @@ def main():
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = ab / avg_s / 1e9 if avg_s > 0 else 0.0
     roofline = {"bound": "hbm", "kernel": KID_NAMES[kid], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "algorithmic_bytes_per_launch": ab,
+                "frac": achieved / peak, "traffic": recorded_traffic(kid) if args.workload == "constriction_3d" else None,
+                "algorithmic_bytes_per_launch": ab,
                 "avg_launch_us": avg_s * 1e3 * 1e3, "launches_in_timed_region": per_class_launches[kid],
                 "share_of_step": prof[kid][1] / ms if ms > 0 else None,
                 "classes": {KID_NAMES[k]: {"avg_us": prof[k][0] * 1e3, "est_share": prof[k][1] / ms}
