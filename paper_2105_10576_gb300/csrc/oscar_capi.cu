@@ -264,12 +264,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
         int by = 256 / bx;
         long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
         I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
-        int cta_cells = 1024;
-        const char *e = getenv("OSCAR_CTA_CELLS");
-        if (e) cta_cells = atoi(e) > 0 && atoi(e) <= 1024 ? atoi(e) : cta_cells;
-        I.lc0 = I.nlev - 1;
-        while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= cta_cells) --I.lc0;
-        if (I.nlev - I.lc0 > 16) I.lc0 = I.nlev - 16;
+        I.lc0 = I.nlev - 1;   // refined by the solver set-up (shared-memory budget of the coarse CTA)
         const char *enu = getenv("OSCAR_MG_NU");
         if (enu && atoi(enu) >= 1 && atoi(enu) <= 4) I.mg_nu = atoi(enu);
         const char *enc = getenv("OSCAR_MG_NUC");

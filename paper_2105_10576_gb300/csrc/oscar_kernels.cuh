@@ -35,10 +35,13 @@ constexpr int BS = 256;
 constexpr int kCtaCells = 1024;      // levels at or below this size run in one CTA
 constexpr int kMaxCL = 16;
 
-// Programmatic dependent launch: every kernel is launched so that it may start
-// while its predecessor drains; it waits here, before touching any memory, for
-// the predecessor to complete and its writes to be visible.
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Programmatic dependent launch: wait until the preceding kernel has
+// completed and its writes are visible, then let the next kernel's CTAs be
+// scheduled (they in turn wait here), so its launch overlaps this one.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ int ftype(uint32_t info, int a, int s) { return (info >> (3 * (2 * a + s))) & 7; }
 
@@ -95,6 +98,17 @@ inline L3 launch3(int nx, int ny, int nz) {
 }
 inline L3 launch3(const GridH &g) { return launch3(g.nx, g.ny, g.nz); }
 inline L3 launch3_faces(const GridH &g, int a) { return launch3(g.nx + (a == 0), g.ny + (a == 1), g.nz + (a == 2)); }
+// blocks of launch3's shape over (x, rows); about target blocks, each thread
+// taking m rows (ROW_LOOP)
+inline L3 launch_rows(const GridH &g, int target) {
+    L3 l = launch3(g.nx, g.ny * g.nz, 1);
+    int gx = (int)l.grid.x, gy = (int)l.grid.y;
+    int want = target / gx > 0 ? target / gx : 1;
+    int m = (gy + want - 1) / want;
+    l.grid = dim3(gx, (gy + m - 1) / m, 1);
+    l.nblocks = (int)(l.grid.x * l.grid.y);
+    return l;
+}
 
 #define CELL_IJK(g)                                            \
     const int i = blockIdx.x * blockDim.x + threadIdx.x;       \
@@ -104,6 +118,17 @@ inline L3 launch3_faces(const GridH &g, int a) { return launch3(g.nx + (a == 0),
     const int c = i + (g).nx * (j + (g).ny * k);
 
 #define BLOCK_ID() ((int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)))
+
+// Row loop of the stencil reductions (launch_rows): the thread at x = i takes
+// every (gridDim.y * blockDim.y)-th row, row = j + ny k, so that a thread sums
+// several cells before the block reduction.
+#define ROW_LOOP(g)                                              \
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;         \
+    const int nrow_ = (g).ny * (g).nz;                           \
+    for (int row = blockIdx.y * blockDim.y + threadIdx.y; row < nrow_; row += gridDim.y * blockDim.y)
+#define ROW_CELL(g)                                              \
+    const int k = row / (g).ny, j = row - k * (g).ny;            \
+    const int c = i + (g).nx * row;
 
 __device__ __forceinline__ int flo(const GridD &g, int a, int i, int j, int k) {
     if (a == 0) return i + (g.nx + 1) * (j + g.ny * k);
@@ -153,36 +178,29 @@ __device__ __forceinline__ int decode_face(const GridD &g, const uint32_t *__res
 // ---------------------------------------------------------------------------
 // reductions (one partial per block, finished in one block: deterministic)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum(double v) {
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int t = threadIdx.x + blockDim.x * threadIdx.y;
-    int w = t >> 5, l = t & 31;
+// Block reductions, deterministic, result valid in thread 0. The per-thread
+// values pass through shared memory and only warp 0 does FP64 arithmetic:
+// GB300 issues FP64 at a small fraction of its FP32 rate, and a shuffle tree
+// in every warp made FP64 the bottleneck of the vector kernels.
+__device__ __forceinline__ double block_reduce(double v, bool is_max) {
+    __shared__ double sh[1024];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    __syncthreads();   // a previous reduction's readers are done with sh
+    sh[t] = v;
     __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    int nw = (blockDim.x * blockDim.y) >> 5;
-    if (w == 0) {
-        v = l < nw ? sh[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (t < 32) {
+        double s = t < nt ? sh[t] : 0.0;
+        for (int q = t + 32; q < nt; q += 32) s = is_max ? fmax(s, sh[q]) : s + sh[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            double w = __shfl_down_sync(0xffffffffu, s, o);
+            s = is_max ? fmax(s, w) : s + w;
+        }
+        v = s;
     }
     return v;
 }
-__device__ __forceinline__ double block_max(double v) {
-    __shared__ double sh[32];
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    int t = threadIdx.x + blockDim.x * threadIdx.y;
-    int w = t >> 5, l = t & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    int nw = (blockDim.x * blockDim.y) >> 5;
-    if (w == 0) {
-        v = l < nw ? sh[l] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
-    }
-    return v;
-}
+__device__ __forceinline__ double block_sum(double v) { return block_reduce(v, false); }
+__device__ __forceinline__ double block_max(double v) { return block_reduce(v, true); }
 __device__ __forceinline__ bool block_leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
 // Single-pass reduction: every block stores its partial(s); the block that
@@ -754,16 +772,17 @@ __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
                           const double *__restrict__ b, double *__restrict__ scal, double inv_nf,
                           double *__restrict__ part, int stride, unsigned *__restrict__ ticket, int nb) {
     griddep_wait();
-    CELL_IJK(g);
     double qbar = scal[S_QSUM] * inv_nf;
     double res = 0.0, nrm = 0.0;
-    if (inside) {
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
         uint32_t inf = info[c];
         if (inf & INFO_FLUID) {
             double Mq = poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
             double Mqbar = qbar * outlet_coeff<T>(g, inf, i, j, k, cf);
-            res = fabs(b[c] - Mq);
-            nrm = fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
+            res += fabs(b[c] - Mq);
+            nrm += fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
         }
     }
     if (reduce_last(res, nrm, 2, false, part, stride, ticket, nb) && block_leader()) {
@@ -851,16 +870,18 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
                               double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
                               int *__restrict__ ctl, int mode, double tol, double invU, cudaGraphConditionalHandle h) {
     griddep_wait();
-    double m = 0.0, dummy = 0.0;
+    T mt = T(0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
         if (!(info[c] & INFO_FLUID)) continue;
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            double x = (double)v.a[a][c];
-            usum.a[a][c] += x;
-            m = fmax(m, fabs(x - (double)vold.a[a][c]));
+            T x = v.a[a][c];
+            usum.a[a][c] += (double)x;
+            T d = x - vold.a[a][c];
+            mt = d > mt ? d : (-d > mt ? -d : mt);
         }
     }
+    double m = (double)mt, dummy = 0.0;
     if (reduce_last(m, dummy, 1, true, part, 0, ticket, gridDim.x) && block_leader()) {
         scal[S_DUMAX] = m;
         int k = ++ctl[C_K];
@@ -878,8 +899,8 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 // ---------------------------------------------------------------------------
 // CG. The residual of the outer (FP64) system is r = b - M q with q and b in
 // FP64; the Krylov vectors are of type V (double on the FP64 path, float on
-// the mixed path). Dot products are accumulated per thread in V and across
-// threads and blocks in FP64; the finishing block of each reduction also
+// the mixed path). Dot products are accumulated per thread in V (a thread
+// takes several cells) and across threads and blocks in FP64; the finishing block of each reduction also
 // computes the CG scalars and takes the loop decisions.
 // ---------------------------------------------------------------------------
 template <int DIM, typename T, typename V>
@@ -888,17 +909,19 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
                           unsigned *__restrict__ ticket, int nb, double *__restrict__ scal, int *__restrict__ ctl,
                           double rtol, int mode, cudaGraphConditionalHandle h) {
     griddep_wait();
-    CELL_IJK(g);
     double bb = 0.0, rr = 0.0;
-    if (inside) {
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
         uint32_t inf = info[c];
         if (!(inf & INFO_FLUID)) {
             r[c] = V(0);
         } else {
-            double rc = b[c] - poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
+            double bc = b[c];
+            double rc = bc - poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
             r[c] = (V)rc;
-            bb = b[c] * b[c];
-            rr = rc * rc;
+            bb += bc * bc;
+            rr += rc * rc;
         }
     }
     if (reduce_last(bb, rr, 2, false, part, stride, ticket, nb) && block_leader()) {
@@ -914,18 +937,20 @@ __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T>
                                V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket, int nb,
                                double *__restrict__ scal) {
     griddep_wait();
-    CELL_IJK(g);
-    double acc = 0.0, dummy = 0.0;
-    if (inside) {
+    V accv = V(0);
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
         uint32_t inf = info[c];
         if (!(inf & INFO_FLUID)) {
             Ap[c] = V(0);
         } else {
             V y = poisson_row<DIM, T, V>(g, inf, c, i, j, k, cf, p);
             Ap[c] = y;
-            acc = (double)(p[c] * y);
+            accv += p[c] * y;
         }
     }
+    double acc = (double)accv, dummy = 0.0;
     if (reduce_last(acc, dummy, 1, false, part, 0, ticket, nb) && block_leader()) {
         scal[S_PAP] = acc;
         scal[S_ALPHA] = scal[S_RZ1] / acc;
@@ -1126,113 +1151,247 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
     diag[c] = acc;
 }
 
-// The V-cycle on the coarse levels (at most 1024 cells each) in one CTA of
-// 1024 threads, one cell per thread, with every level held in shared memory;
-// the same symmetric schedule as the per-level kernels (pre-smoothing
+// The V-cycle on the coarse levels in one CTA, with every level held in
+// shared memory. The face coefficients are copied in asynchronously
+// (cp.async) and rearranged once per launch into per-cell form: the six
+// neighbour coefficients (zero across the domain boundary), the diagonal
+// (sum of the six face coefficients, as k_mg_diag) and its reciprocal, the
+// packed cell coordinates and, per colour, the list of fluid cells. x carries
+// a zero pad of one plane on each side, so the stencil reads need no bounds
+// tests. A smoothing step is then a handful of shared-memory loads and FMAs
+// per cell. Same symmetric schedule as the per-level kernels (pre-smoothing
 // red-black, post-smoothing black-red, symmetric sweeps on the coarsest
-// level). Reads b of its top level from global memory, writes x back.
+// level); the residual for the restriction is formed cell-parallel first.
+constexpr int kCtaThreads = 1024;
 template <typename M> struct CLevel {
     GridD g;
-    const M *c[3];     // global face coefficients
-    const M *diag;
+    const M *c[3];          // global face coefficients
     const uint8_t *fluid;
-    int r[3];          // ratios to the next level
-    int ox, ob, od, oc[3], ofl, opk;   // shared-memory offsets (bytes); opk: packed i | j<<10 | k<<20
+    int r[3];               // ratios to the next level (1 or 2)
+    float rnx, rny, rhx;    // 1/nx, 1/ny, 1/ceil(nx/2) for the cell decomposition
+    int nh;                 // entries of a colour list: ceil(nx/2) ny nz
+    // shared-memory byte offsets: x (past its pad), b, diagonal, reciprocal,
+    // neighbour coefficients (2 DIM per cell), packed coordinates, colour
+    // lists, fluid flags, staging of the face arrays
+    int ox, ob, od, oi, ow, opk, ol[2], ofl, os[3];
 };
 template <typename M> struct CLevels {
     int n, nu, nu_top, coarse_sweeps;
+    int ors;           // residual scratch (cells of the largest level)
     const M *b_top;    // global b of the top level
     M *x_top;          // global x of the top level
     CLevel<M> L[kMaxCL];
 };
 
-template <int DIM, typename M>
-__device__ __forceinline__ void cta_sweep(const CLevel<M> &L, unsigned char *sm, int colour) {
-    const GridD &g = L.g;
-    M *x = (M *)(sm + L.ox);
-    const M *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
-    const uint8_t *fl = sm + L.ofl;
-    MG3<M> cc;
-    for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
-    int cell = threadIdx.x;
-    if (cell < g.ncell) {
-        int pk = ((const int *)(sm + L.opk))[cell];
-        int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
-        if (((i + j + k) & 1) == colour && fl[cell] && d[cell] > M(0))
-            x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d[cell];
-    }
-    __syncthreads();
+// idx -> (a, b, c) with idx = a + n0 * (b + n1 * c), without integer
+// division (float reciprocals, corrected by one step; exact below 2^22)
+__device__ __forceinline__ void split3(int idx, int n0, float rn0, int n1, float rn1, int &a, int &b, int &c) {
+    int r = (int)(((float)idx + 0.5f) * rn0);
+    a = idx - r * n0;
+    if (a < 0) { --r; a += n0; } else if (a >= n0) { ++r; a -= n0; }
+    c = (int)(((float)r + 0.5f) * rn1);
+    b = r - c * n1;
+    if (b < 0) { --c; b += n1; } else if (b >= n1) { ++c; b -= n1; }
 }
 
+template <int B> struct CpAsync;
+template <> struct CpAsync<4> {
+    __device__ static __forceinline__ void copy(void *dst, const void *src) {
+        unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(src) : "memory");
+    }
+};
+template <> struct CpAsync<8> {
+    __device__ static __forceinline__ void copy(void *dst, const void *src) {
+        unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+    }
+};
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+constexpr uint32_t kPkFluid = 1u << 31;
+__device__ __forceinline__ void pk_ijk(uint32_t pk, int &i, int &j, int &k) {
+    i = (int)(pk & 1023u);
+    j = (int)((pk >> 10) & 1023u);
+    k = (int)((pk >> 20) & 1023u);
+}
+
+// sum of the neighbour terms of one row
 template <int DIM, typename M>
-__global__ void __launch_bounds__(1024) k_mg_coarse(CLevels<M> P) {
+__device__ __forceinline__ M cta_off(const M *__restrict__ w, const M *x, int cell, int nx, int nxy) {
+    M off = w[0] * x[cell - 1] + w[1] * x[cell + 1];
+    off += w[2] * x[cell - nx] + w[3] * x[cell + nx];
+    if (DIM == 3) off += w[4] * x[cell - nxy] + w[5] * x[cell + nxy];
+    return off;
+}
+
+// one colour of a red-black sweep, by threads t0, t0 + st, ... (no barrier)
+template <int DIM, typename M>
+__device__ __forceinline__ void cta_sweep(const CLevel<M> &L, unsigned char *sm, int colour, int t0, int st) {
+    M *x = (M *)(sm + L.ox);
+    const M *b = (const M *)(sm + L.ob), *iv = (const M *)(sm + L.oi), *w = (const M *)(sm + L.ow);
+    const unsigned short *lst = (const unsigned short *)(sm + L.ol[colour]);
+    const int nx = L.g.nx, nxy = L.g.nx * L.g.ny;
+    for (int h = t0; h < L.nh; h += st) {
+        const int cell = lst[h];
+        if (cell == 0xFFFF) continue;
+        x[cell] = (b[cell] + cta_off<DIM, M>(w + 2 * DIM * cell, x, cell, nx, nxy)) * iv[cell];
+    }
+}
+
+// Levels of at most this many cells are worked by warp 0 alone, with warp
+// barriers between their phases instead of block barriers.
+constexpr int kWarpCells = 128;
+
+template <int DIM, typename M>
+__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char sm[];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, nt = blockDim.x;
+    // 1. loads: face arrays and b of the top level asynchronously, fluid
+    //    flags directly; x (with pads) and the coarser b cleared
     for (int l = 0; l < P.n; ++l) {
         const CLevel<M> &L = P.L[l];
         const GridD &g = L.g;
-        int nf[3] = {(g.nx + 1) * g.ny * g.nz, g.nx * (g.ny + 1) * g.nz, g.nx * g.ny * (g.nz + 1)};
-        for (int a = 0; a < DIM; ++a)
-            for (int q = t; q < nf[a]; q += blockDim.x) ((M *)(sm + L.oc[a]))[q] = L.c[a][q];
-        if (t < g.ncell) {
-            int r = t / g.nx;
-            ((int *)(sm + L.opk))[t] = (t - r * g.nx) | ((r % g.ny) << 10) | ((r / g.ny) << 20);
-            ((M *)(sm + L.od))[t] = L.diag[t];
-            (sm + L.ofl)[t] = L.fluid[t];
-            ((M *)(sm + L.ox))[t] = M(0);
-            ((M *)(sm + L.ob))[t] = l == 0 ? P.b_top[t] : M(0);
+        const int nf[3] = {(g.nx + 1) * g.ny * g.nz, g.nx * (g.ny + 1) * g.nz, g.nx * g.ny * (g.nz + 1)};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            M *dst = (M *)(sm + L.os[a]);
+            for (int q = t; q < nf[a]; q += nt) CpAsync<sizeof(M)>::copy(dst + q, L.c[a] + q);
+        }
+        if (l == 0)
+            for (int q = t; q < g.ncell; q += nt) CpAsync<sizeof(M)>::copy((M *)(sm + L.ob) + q, P.b_top + q);
+    }
+    for (int l = 0; l < P.n; ++l) {
+        const CLevel<M> &L = P.L[l];
+        const int n = L.g.ncell, pad = L.g.nx * L.g.ny;
+        for (int q = t; q < n; q += nt) (sm + L.ofl)[q] = L.fluid[q];
+        M *x = (M *)(sm + L.ox);
+        for (int q = t - pad; q < n + pad; q += nt) x[q] = M(0);
+        if (l > 0)
+            for (int q = t; q < n; q += nt) ((M *)(sm + L.ob))[q] = M(0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // 2. per-cell form
+    for (int l = 0; l < P.n; ++l) {
+        const CLevel<M> &L = P.L[l];
+        const GridD &g = L.g;
+        const uint8_t *fl = sm + L.ofl;
+        for (int q = t; q < g.ncell; q += nt) {
+            int i, j, k;
+            split3(q, g.nx, L.rnx, g.ny, L.rny, i, j, k);
+            const int ijk[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+            M *w = (M *)(sm + L.ow) + 2 * DIM * q;
+            M d = M(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const M *cc = (const M *)(sm + L.os[a]);
+                const M cl = cc[flo(g, a, i, j, k)], ch = cc[fhi(g, a, i, j, k)];
+                d += cl + ch;
+                w[2 * a] = ijk[a] > 0 ? cl : M(0);
+                w[2 * a + 1] = ijk[a] < n[a] - 1 ? ch : M(0);
+            }
+            ((M *)(sm + L.od))[q] = d;
+            ((M *)(sm + L.oi))[q] = d > M(0) ? M(1) / d : M(0);
+            ((uint32_t *)(sm + L.opk))[q] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20) | (fl[q] ? kPkFluid : 0u);
+        }
+        const int hx = (g.nx + 1) >> 1;
+        for (int h = t; h < L.nh; h += nt) {
+            int ti, j, k;
+            split3(h, hx, L.rhx, g.ny, L.rny, ti, j, k);
+#pragma unroll
+            for (int colour = 0; colour < 2; ++colour) {
+                const int i = 2 * ti + ((j + k + colour) & 1);
+                const int cell = i + g.nx * (j + g.ny * k);
+                ((unsigned short *)(sm + L.ol[colour]))[h] = (i < g.nx && fl[cell]) ? (unsigned short)cell : 0xFFFF;
+            }
         }
     }
-    __syncthreads();
+    // phase bookkeeping: a block barrier wherever this or the previous phase
+    // involves the whole block, a warp barrier between two warp-0 phases
+    bool prev_blk = true;
+    int t0 = t, st = nt;
+    bool active = true;
+#define phase(L)                                                   \
+    do {                                                           \
+        const bool blk_ = (L).g.ncell > kWarpCells;                \
+        if (prev_blk || blk_) __syncthreads(); else __syncwarp();  \
+        prev_blk = blk_;                                           \
+        st = blk_ ? nt : 32;                                       \
+        active = blk_ || t < 32;                                   \
+    } while (0)
+    M *rs = (M *)(sm + P.ors);
     for (int l = 0; l < P.n - 1; ++l) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
         const int nu = l == 0 ? P.nu_top : P.nu;
-        for (int s = 0; s < nu; ++s) { cta_sweep<DIM, M>(L, sm, 0); cta_sweep<DIM, M>(L, sm, 1); }
-        const M *x = (const M *)(sm + L.ox), *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
-        const uint8_t *fl = sm + L.ofl;
-        MG3<M> cc;
-        for (int a = 0; a < 3; ++a) cc.a[a] = (const M *)(sm + L.oc[a]);
-        if (t < C.g.ncell) {
-            int pk = ((const int *)(sm + C.opk))[t];
-            int I = pk & 1023, J = (pk >> 10) & 1023, K = pk >> 20;
-            M acc = M(0);
-            for (int oz = 0; oz < L.r[2]; ++oz) {
-                int kk = K * L.r[2] + oz;
-                if (kk >= L.g.nz) break;
-                for (int oy = 0; oy < L.r[1]; ++oy) {
-                    int jj = J * L.r[1] + oy;
-                    if (jj >= L.g.ny) break;
-                    for (int ox = 0; ox < L.r[0]; ++ox) {
-                        int ii = I * L.r[0] + ox;
-                        if (ii >= L.g.nx) break;
-                        int cell = ii + L.g.nx * (jj + L.g.ny * kk);
-                        if (!fl[cell]) continue;
-                        acc += b[cell] - (d[cell] * x[cell] - mg_offdiag<DIM, M>(L.g, cc, x, cell, ii, jj, kk));
-                    }
-                }
-            }
-            ((M *)(sm + C.ob))[t] = acc;
+        for (int s = 0; s < nu; ++s) {
+            phase(L); if (active) cta_sweep<DIM, M>(L, sm, 0, t0, st);
+            phase(L); if (active) cta_sweep<DIM, M>(L, sm, 1, t0, st);
         }
-        __syncthreads();
+        phase(L);
+        if (active) {   // residual b - M x, cell-parallel
+            const M *x = (const M *)(sm + L.ox), *b = (const M *)(sm + L.ob), *d = (const M *)(sm + L.od);
+            const M *w = (const M *)(sm + L.ow);
+            const uint32_t *pk = (const uint32_t *)(sm + L.opk);
+            const int nx = L.g.nx, nxy = L.g.nx * L.g.ny;
+            for (int q = t0; q < L.g.ncell; q += st)
+                rs[q] = (pk[q] & kPkFluid) ? b[q] - (d[q] * x[q] - cta_off<DIM, M>(w + 2 * DIM * q, x, q, nx, nxy)) : M(0);
+        }
+        phase(L);
+        if (active) {   // restriction: sum over the children
+            const uint32_t *pkc = (const uint32_t *)(sm + C.opk);
+            M *bc = (M *)(sm + C.ob);
+            const int nx = L.g.nx, ny = L.g.ny, nz = L.g.nz;
+            for (int q = t0; q < C.g.ncell; q += st) {
+                int I, J, K;
+                pk_ijk(pkc[q], I, J, K);
+                const int i0 = I * L.r[0], j0 = J * L.r[1], k0 = K * L.r[2];
+                const int i1 = min(i0 + L.r[0], nx), j1 = min(j0 + L.r[1], ny), k1 = min(k0 + L.r[2], nz);
+                M acc = M(0);
+                for (int kk = k0; kk < k1; ++kk)
+                    for (int jj = j0; jj < j1; ++jj)
+                        for (int ii = i0; ii < i1; ++ii) acc += rs[ii + nx * (jj + ny * kk)];
+                bc[q] = acc;
+            }
+        }
     }
     const CLevel<M> &Lc = P.L[P.n - 1];
-    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, sm, 0); cta_sweep<DIM, M>(Lc, sm, 1); }
-    for (int s = 0; s < P.coarse_sweeps; ++s) { cta_sweep<DIM, M>(Lc, sm, 1); cta_sweep<DIM, M>(Lc, sm, 0); }
+    for (int s = 0; s < P.coarse_sweeps; ++s) {
+        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
+        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
+    }
+    for (int s = 0; s < P.coarse_sweeps; ++s) {
+        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
+        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
+    }
     for (int l = P.n - 2; l >= 0; --l) {
         const CLevel<M> &L = P.L[l];
         const CLevel<M> &C = P.L[l + 1];
-        if (t < L.g.ncell && (sm + L.ofl)[t]) {
-            int pk = ((const int *)(sm + L.opk))[t];
-            int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
-            ((M *)(sm + L.ox))[t] += ((const M *)(sm + C.ox))[(i / L.r[0]) + C.g.nx * ((j / L.r[1]) + C.g.ny * (k / L.r[2]))];
+        phase(L);
+        if (active) {   // prolongation (piecewise constant)
+            const uint32_t *pk = (const uint32_t *)(sm + L.opk);
+            const M *xc = (const M *)(sm + C.ox);
+            M *x = (M *)(sm + L.ox);
+            const int s0 = L.r[0] >> 1, s1 = L.r[1] >> 1, s2 = L.r[2] >> 1;
+            for (int q = t0; q < L.g.ncell; q += st) {
+                const uint32_t v = pk[q];
+                if (!(v & kPkFluid)) continue;
+                int i, j, k;
+                pk_ijk(v, i, j, k);
+                x[q] += xc[(i >> s0) + C.g.nx * ((j >> s1) + C.g.ny * (k >> s2))];
+            }
         }
-        __syncthreads();
         const int nu = l == 0 ? P.nu_top : P.nu;
-        for (int s = 0; s < nu; ++s) { cta_sweep<DIM, M>(L, sm, 1); cta_sweep<DIM, M>(L, sm, 0); }
+        for (int s = 0; s < nu; ++s) {
+            phase(L); if (active) cta_sweep<DIM, M>(L, sm, 1, t0, st);
+            phase(L); if (active) cta_sweep<DIM, M>(L, sm, 0, t0, st);
+        }
     }
-    if (t < P.L[0].g.ncell) P.x_top[t] = ((const M *)(sm + P.L[0].ox))[t];
+#undef phase
+    __syncthreads();
+    for (int q = t; q < P.L[0].g.ncell; q += nt) P.x_top[q] = ((const M *)(sm + P.L[0].ox))[q];
 }
 
 }  // namespace oscar

@@ -10,6 +10,7 @@
 // defect-correction WHILE loop. Graphs are captured from the same launch
 // sequence the eager mode issues, and rebuilt when the time step changes.
 #pragma once
+#include <stdlib.h>
 #include <string.h>
 
 #include "oscar_kernels.cuh"
@@ -240,31 +241,42 @@ template <typename T> struct Impl {
         return 0;
     }
 
-    // levels lc0.. of the single-CTA coarse kernel with their shared-memory layout
-    static size_t cta_levels(Instance &I, CLevels<M> &P) {
-        P.n = I.nlev - I.lc0;
+    // levels l0.. of the single-CTA coarse kernel with their shared-memory
+    // layout; returns the bytes of shared memory they need
+    static size_t cta_levels(Instance &I, CLevels<M> &P, int l0) {
+        P.n = I.nlev - l0;
         P.nu = I.mg_nu_c;
-        P.nu_top = I.lc0 == 0 ? I.mg_nu : I.mg_nu_c;
+        P.nu_top = l0 == 0 ? I.mg_nu : I.mg_nu_c;
         P.coarse_sweeps = I.mg_coarse_sweeps;
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
-        for (int q = 0; q < P.n; ++q) {
-            Level &L = I.lev[I.lc0 + q];
+        size_t nmax = 0;
+        for (int q = 0; q < P.n && q < kMaxCL; ++q) {
+            Level &L = I.lev[l0 + q];
             CLevel<M> &C = P.L[q];
             C.g = to_dev(L.g);
             for (int a = 0; a < 3; ++a) C.c[a] = (const M *)L.c[a];
-            C.diag = (const M *)L.diag;
             C.fluid = L.fluid;
             for (int a = 0; a < 3; ++a) C.r[a] = L.r[a];
-            size_t n = L.g.ncell;
-            C.ox = take(n * sizeof(M));
+            C.rnx = 1.0f / (float)L.g.nx;
+            C.rny = 1.0f / (float)L.g.ny;
+            C.rhx = 1.0f / (float)((L.g.nx + 1) / 2);
+            C.nh = ((L.g.nx + 1) / 2) * L.g.ny * L.g.nz;
+            size_t n = L.g.ncell, pad = (size_t)L.g.nx * L.g.ny, dim = L.g.dim;
+            nmax = n > nmax ? n : nmax;
+            C.ox = take((n + 2 * pad) * sizeof(M)) + (int)(pad * sizeof(M));
             C.ob = take(n * sizeof(M));
             C.od = take(n * sizeof(M));
-            for (int a = 0; a < 3; ++a) C.oc[a] = take((size_t)L.g.nf[a] * sizeof(M));
+            C.oi = take(n * sizeof(M));
+            C.ow = take(2 * dim * n * sizeof(M));
+            C.opk = take(n * sizeof(uint32_t));
+            C.ol[0] = take(C.nh * sizeof(unsigned short));
+            C.ol[1] = take(C.nh * sizeof(unsigned short));
             C.ofl = take(n);
-            C.opk = take(n * sizeof(int));
+            for (int a = 0; a < 3; ++a) C.os[a] = take(a < L.g.dim ? (size_t)L.g.nf[a] * sizeof(M) : 0);
         }
-        return off;
+        P.ors = take(nmax * sizeof(M));
+        return P.n > kMaxCL ? (size_t)-1 : off;
     }
 
     // x / b of level l (level 0 works in place on the Krylov vectors z / r)
@@ -323,10 +335,10 @@ template <typename T> struct Impl {
             prof_end(I, ps);
         }
         CLevels<M> P;
-        cta_levels(I, P);
+        cta_levels(I, P, I.lc0);
         P.b_top = lb(I, I.lc0, r);
         P.x_top = lx(I, I.lc0, z);
-        launchk(k_mg_coarse<DIM, M>, 1, 1024, I.cta_smem, I.stream, P), ++I.nlaunch;
+        launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P), ++I.nlaunch;
         for (int l = I.lc0 - 1; l >= 0; --l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -346,7 +358,7 @@ template <typename T> struct Impl {
     template <int DIM>
     static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h) {
         GridD g = to_dev(I.g);
-        L3 L = launch3(I.g);
+        L3 L = launch_rows(I.g, kRedBlocks);
         launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, I.partials,
                                                                I.red_stride, I.ticket, L.nblocks, I.scal, I.ctl,
                                                                I.P.cg_rtol, mode, h), ++I.nlaunch;
@@ -356,7 +368,7 @@ template <typename T> struct Impl {
     template <int DIM>
     static int pcg_body(Instance &I, V *x, int target_slot, cudaGraphConditionalHandle h) {
         GridD g = to_dev(I.g);
-        L3 L = launch3(I.g);
+        L3 L = launch_rows(I.g, kRedBlocks);
         int n = I.g.ncell;
         V *r = (V *)I.cg_r, *z = (V *)I.cg_z, *p = (V *)I.cg_p, *Ap = (V *)I.cg_Ap;
         long long n0 = I.nlaunch;
@@ -451,9 +463,10 @@ template <typename T> struct Impl {
             if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
                 launchk(k_sum_to<double>, kRedBlocks, BS, 0, I.stream, g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
                                                                   S_QSUM), ++I.nlaunch;
-                launchk(k_normres<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(cf), q, I.cg_b, I.scal,
+                L3 LR = launch_rows(I.g, kRedBlocks);
+                launchk(k_normres<DIM, T>, LR.grid, LR.block, 0, I.stream, g, I.info, c3(cf), q, I.cg_b, I.scal,
                                                                     1.0 / (double)I.n_fluid, I.partials, I.red_stride,
-                                                                    I.ticket, L.nblocks), ++I.nlaunch;
+                                                                    I.ticket, LR.nblocks), ++I.nlaunch;
             }
             OSCAR_LAUNCH_CHECK();
             OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
@@ -671,9 +684,17 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                                                                F.fluid, Lv.fluid), ++I.nlaunch;
     }
     OSCAR_LAUNCH_CHECK();
+    // the coarse CTA takes the levels of at most 1024 cells (one per thread;
+    // larger levels ran faster as separate launches) whose subtree fits the
+    // shared-memory budget; OSCAR_CTA_CELLS moves the cap, for tuning
     CLevels<T> P;
-    I.cta_smem = Impl<T>::cta_levels(I, P);
-    if (I.lev[I.lc0].g.ncell > 1024 || I.cta_smem > 200 * 1024) return OSCAR_E_INVALID_ARG;
+    const size_t budget = 224 * 1024;
+    long long cap = 1024;
+    if (const char *e = getenv("OSCAR_CTA_CELLS")) cap = atoll(e) > 0 ? atoll(e) : cap;
+    I.lc0 = I.nlev - 1;
+    while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= cap && Impl<T>::cta_levels(I, P, I.lc0 - 1) <= budget) --I.lc0;
+    I.cta_smem = Impl<T>::cta_levels(I, P, I.lc0);
+    if (I.cta_smem > budget) return OSCAR_E_INVALID_ARG;
     cudaError_t e = I.g.dim == 3 ? cudaFuncSetAttribute(k_mg_coarse<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)I.cta_smem)
                                  : cudaFuncSetAttribute(k_mg_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -713,7 +734,7 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OSCAR_E_CUDA;
     GridD g = to_dev(I.g);
-    L3 L = launch3(I.g);
+    L3 L = launch3(I.g), LR = launch_rows(I.g, kRedBlocks);
     double dt = I.last_dt > 0 ? I.last_dt : 1e-7;
     Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
     Level &L0 = I.lev[0];
@@ -731,12 +752,12 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
             }
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)
-                launchk(k_cg_apply_dot<3, T, V>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
+                launchk(k_cg_apply_dot<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                                                                          (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks,
                                                                           I.scal), ++I.nlaunch;
             else
-                launchk(k_cg_apply_dot<2, T, V>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, I.partials, I.ticket, L.nblocks,
+                launchk(k_cg_apply_dot<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
+                                                                          (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks,
                                                                           I.scal), ++I.nlaunch;
         } else if (kid == OSCAR_KID_MOMENTUM) {
             C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
