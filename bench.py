@@ -63,10 +63,10 @@ def algorithmic_bytes(kid: int, c, es: int) -> float:
     nf = (p["nx"] + 1) * p["ny"] * (p["nz"] if d == 3 else 1) + p["nx"] * (p["ny"] + 1) * (p["nz"] if d == 3 else 1)
     if d == 3:
         nf += p["nx"] * p["ny"] * (p["nz"] + 1)
-    if kid == 0:   # RB-GS half sweep: x (all) + b, diag, fluid (half) + face coeffs (each face once) + x write (half)
-        return n * (es + 0.5 * (2 * es + 1) + 0.5 * es) + nf * es
-    if kid == 1:   # operator apply + dot: p (8) read, Ap (8) write, info (4), face coeffs once
-        return n * (8 + 8 + 4) + nf * es
+    if kid == 0:   # RB-GS half sweep: x (all) + b, 1/diag (half) + face coeffs (each face once) + x write (half)
+        return n * (es + 0.5 * (2 * es) + 0.5 * es) + nf * es
+    if kid == 1:   # operator apply + dot: p read, Ap write, info (4), face coeffs once
+        return n * (es + es + 4) + nf * es
     if kid == 2:   # HbyA: v, vold, hbya (d each), alpha, rA, G (d*d), info; phic faces once
         return n * (es * (3 * d + 2 + d * d) + 4) + nf * es
     if kid == 3:   # transport (3 kernels): low, ratio, update
@@ -74,8 +74,15 @@ def algorithmic_bytes(kid: int, c, es: int) -> float:
         ratio = n * (4 * es + 4 + 2 * es)
         upd = n * (4 * es + 4 + es) + 2 * nf * es
         return low + ratio + upd
-    if kid == 4:   # MG residual: x, b, diag, fluid, res + face coeffs once
-        return n * (4 * es + 1) + nf * es
+    if kid == 4:   # MG residual + restriction: x, b, diag, fluid + coarse b, x (n / R cells) + face coeffs once
+        h = [p["hx"], p["hy"], p["hz"]][:d]
+        dims = [p["nx"], p["ny"], p["nz"]][:d]
+        hmin = min(hh for hh, nn in zip(h, dims) if nn > 1)
+        R = 1
+        for hh, nn in zip(h, dims):
+            if nn > 1 and hh < 2 * hmin:
+                R *= 2
+        return n * (3 * es + 1) + (n / R) * 2 * es + nf * es
     raise ValueError(kid)
 
 

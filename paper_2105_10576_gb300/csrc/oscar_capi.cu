@@ -160,6 +160,7 @@ static void carve(Instance &I, Carver &C) {
         L.fluid = (uint8_t *)C.take(n);
         for (int a = 0; a < 3; ++a) L.c[a] = C.take((size_t)L.g.nf[a] * es);
         L.diag = C.take(n * es);
+        L.idiag = C.take(n * es);
         L.x = C.take(n * es);
         L.b = C.take(n * es);
         L.res = C.take(n * es);

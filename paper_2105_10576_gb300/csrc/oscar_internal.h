@@ -46,6 +46,7 @@ struct Level {
     uint8_t *fluid;      // level >= 1: any fine child fluid
     void *c[3];          // face coefficients (T)
     void *diag;          // T
+    void *idiag;         // T: 1 / diag on fluid cells, else 0
     void *x, *b, *res;   // T
 };
 

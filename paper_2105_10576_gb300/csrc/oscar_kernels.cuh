@@ -903,26 +903,34 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 // takes several cells) and across threads and blocks in FP64; the finishing block of each reduction also
 // computes the CG scalars and takes the loop decisions.
 // ---------------------------------------------------------------------------
+// The kernel also starts the first V-cycle: z receives the colour-0 half
+// sweep of the finest level from z = 0 (z = r / diagonal on colour 0, 0 on
+// colour 1), and the Krylov vectors named in zero1 / zero2 (may be null) are
+// cleared.
 template <int DIM, typename T, typename V>
 __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
-                          const double *__restrict__ b, V *__restrict__ r, double *__restrict__ part, int stride,
-                          unsigned *__restrict__ ticket, int nb, double *__restrict__ scal, int *__restrict__ ctl,
-                          double rtol, int mode, cudaGraphConditionalHandle h) {
+                          const double *__restrict__ b, V *__restrict__ r, const V *__restrict__ idiag0,
+                          V *__restrict__ z, V *__restrict__ zero1, V *__restrict__ zero2, double *__restrict__ part,
+                          int stride, unsigned *__restrict__ ticket, int nb, double *__restrict__ scal,
+                          int *__restrict__ ctl, double rtol, int mode, cudaGraphConditionalHandle h) {
     griddep_wait();
     double bb = 0.0, rr = 0.0;
     ROW_LOOP(g) {
         ROW_CELL(g);
         if (i >= g.nx) continue;
         uint32_t inf = info[c];
-        if (!(inf & INFO_FLUID)) {
-            r[c] = V(0);
-        } else {
+        V rv = V(0);
+        if (inf & INFO_FLUID) {
             double bc = b[c];
             double rc = bc - poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
-            r[c] = (V)rc;
+            rv = (V)rc;
             bb += bc * bc;
             rr += rc * rc;
         }
+        r[c] = rv;
+        z[c] = ((i + j + k) & 1) == 0 ? rv * idiag0[c] : V(0);
+        if (zero1) zero1[c] = V(0);
+        if (zero2) zero2[c] = V(0);
     }
     if (reduce_last(bb, rr, 2, false, part, stride, ticket, nb) && block_leader()) {
         scal[S_BB] = bb;
@@ -957,24 +965,28 @@ __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T>
     }
 }
 
-// x += alpha p, r -= alpha Ap; the finishing block tests ||r|| against
+// x += alpha p, r -= alpha Ap, and z = the first colour-0 half sweep of the
+// next V-cycle (as in k_cg_init); the finishing block tests ||r|| against
 // scal[target_slot] and decides whether the PCG loop continues
 template <typename V>
-__global__ void k_cg_update(int n, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
-                            const V *__restrict__ Ap, double *__restrict__ part, unsigned *__restrict__ ticket,
-                            double *__restrict__ scal, int *__restrict__ ctl, int maxit, int target_slot,
-                            cudaGraphConditionalHandle h) {
+__global__ void k_cg_update(GridD g, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
+                            const V *__restrict__ Ap, const V *__restrict__ idiag0, V *__restrict__ z,
+                            double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
+                            int *__restrict__ ctl, int maxit, int target_slot, cudaGraphConditionalHandle h) {
     griddep_wait();
     const V al = (V)scal[S_ALPHA];
     V accv = V(0);
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
         x[c] += al * p[c];
         V rc = r[c] - al * Ap[c];
         r[c] = rc;
+        z[c] = ((i + j + k) & 1) == 0 ? rc * idiag0[c] : V(0);
         accv += rc * rc;
     }
     double acc = (double)accv, dummy = 0.0;
-    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) {
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x * gridDim.y) && block_leader()) {
         scal[S_RR] = acc;
         int it = ++ctl[C_IT];
         ctl[C_ITSUM] += 1;
@@ -1025,75 +1037,109 @@ __global__ void k_cg_correct(int n, const V *__restrict__ e, double *__restrict_
 // ---------------------------------------------------------------------------
 template <typename M> struct MG3 { const M *a[3]; };
 
+// neighbour coefficients of a row (zero across the domain boundary); the
+// per-level kernels load them, and the other operands that stay fixed during
+// a solve, before griddep_wait, so that only the operands written by the
+// preceding kernel are loaded after it (one round of dependent loads). The
+// coefficient arrays and (inverse) diagonals are written by the set-up of a
+// PISO corrector, never by the kernel that directly precedes a reader.
 template <int DIM, typename M>
-__device__ __forceinline__ M mg_offdiag(const GridD &g, MG3<M> cc, const M *__restrict__ x, int cell, int i, int j,
-                                        int k) {
-    M acc = M(0);
-    int ijk[3] = {i, j, k};
-    int n[3] = {g.nx, g.ny, g.nz};
+__device__ __forceinline__ void mg_row_coeffs(const GridD &g, MG3<M> cc, int i, int j, int k, M *w) {
+    const int ijk[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        int off = noff(g, a);
-        if (ijk[a] > 0) acc += cc.a[a][flo(g, a, i, j, k)] * x[cell - off];
-        if (ijk[a] < n[a] - 1) acc += cc.a[a][fhi(g, a, i, j, k)] * x[cell + off];
+        w[2 * a] = ijk[a] > 0 ? cc.a[a][flo(g, a, i, j, k)] : M(0);
+        w[2 * a + 1] = ijk[a] < n[a] - 1 ? cc.a[a][fhi(g, a, i, j, k)] : M(0);
+    }
+}
+template <int DIM, typename M>
+__device__ __forceinline__ M mg_row_off(const GridD &g, const M *w, const M *x, int cell, int i, int j, int k) {
+    const int ijk[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+    M acc = M(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int off = noff(g, a);
+        if (ijk[a] > 0) acc += w[2 * a] * x[cell - off];
+        if (ijk[a] < n[a] - 1) acc += w[2 * a + 1] * x[cell + off];
     }
     return acc;
 }
 
 // one colour of a red-black Gauss-Seidel sweep; thread ti handles the cell
-// i = 2 ti + ((j + k + colour) & 1) of its row, so no thread idles
+// i = 2 ti + ((j + k + colour) & 1) of its row, so no thread idles. idiag is
+// 1 / diagonal on fluid cells and 0 elsewhere, so solid cells keep x = 0.
 template <int DIM, typename M>
-__global__ void k_mg_rbgs(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, const M *__restrict__ diag,
-                          M *__restrict__ x, const M *__restrict__ b, int colour) {
-    griddep_wait();
+__global__ void k_mg_rbgs(GridD g, MG3<M> cc, const M *__restrict__ idiag, M *__restrict__ x,
+                          const M *__restrict__ b, int colour) {
     const int ti = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     const int i = 2 * ti + ((j + k + colour) & 1);
-    if (i >= g.nx || j >= g.ny) return;
+    const bool ok = i < g.nx && j < g.ny;
     const int cell = i + g.nx * (j + g.ny * k);
-    M d = diag[cell];
-    if (!fluid[cell] || d <= M(0)) return;
-    x[cell] = (b[cell] + mg_offdiag<DIM, M>(g, cc, x, cell, i, j, k)) / d;
+    M w[2 * DIM], id = M(0);
+    if (ok) {
+        mg_row_coeffs<DIM, M>(g, cc, i, j, k, w);
+        id = idiag[cell];
+    }
+    griddep_wait();
+    if (!ok) return;
+    x[cell] = (b[cell] + mg_row_off<DIM, M>(g, w, x, cell, i, j, k)) * id;
 }
 
-// coarse b = sum over children of the fine residual b - M x; coarse x = 0.
-// The coarsening ratios are template parameters so the children unroll and
-// their loads overlap.
+// coarse b = sum over children of the fine residual b - M x. With first set,
+// the coarse x receives the first colour-0 half sweep from x = 0
+// (x = b / diagonal on colour 0, 0 on colour 1), else x = 0. The coarsening
+// ratios are template parameters so the children unroll and their loads
+// overlap.
 template <int DIM, typename M, int RX, int RY, int RZ>
 __global__ void k_mg_resid_restrict(GridD gf, GridD gc, const uint8_t *__restrict__ fluid, MG3<M> cc,
                                     const M *__restrict__ diag, const M *__restrict__ x, const M *__restrict__ b,
-                                    M *__restrict__ bc, M *__restrict__ xc) {
-    griddep_wait();
+                                    M *__restrict__ bc, M *__restrict__ xc, const M *__restrict__ idc, int first) {
     CELL_IJK(gc);
+    constexpr int NCH = RX * RY * RZ;
+    M w[NCH][2 * DIM], dg[NCH];
+    uint8_t fl[NCH];
+    M idq = M(0);
+    if (inside) {
+#pragma unroll
+        for (int q = 0; q < NCH; ++q) {
+            const int ii = i * RX + q % RX, jj = j * RY + (q / RX) % RY, kk = k * RZ + q / (RX * RY);
+            fl[q] = 0;
+            if (ii < gf.nx && jj < gf.ny && kk < gf.nz) {
+                const int cell = ii + gf.nx * (jj + gf.ny * kk);
+                fl[q] = fluid[cell];
+                dg[q] = diag[cell];
+                mg_row_coeffs<DIM, M>(gf, cc, ii, jj, kk, w[q]);
+            }
+        }
+        if (first) idq = idc[c];
+    }
+    griddep_wait();
     if (!inside) return;
     M acc = M(0);
 #pragma unroll
-    for (int oz = 0; oz < RZ; ++oz) {
-#pragma unroll
-        for (int oy = 0; oy < RY; ++oy) {
-#pragma unroll
-            for (int ox = 0; ox < RX; ++ox) {
-                int ii = i * RX + ox, jj = j * RY + oy, kk = k * RZ + oz;
-                if (ii >= gf.nx || jj >= gf.ny || kk >= gf.nz) continue;
-                int cell = ii + gf.nx * (jj + gf.ny * kk);
-                if (!fluid[cell]) continue;
-                acc += b[cell] - (diag[cell] * x[cell] - mg_offdiag<DIM, M>(gf, cc, x, cell, ii, jj, kk));
-            }
-        }
+    for (int q = 0; q < NCH; ++q) {
+        const int ii = i * RX + q % RX, jj = j * RY + (q / RX) % RY, kk = k * RZ + q / (RX * RY);
+        if (ii >= gf.nx || jj >= gf.ny || kk >= gf.nz) continue;
+        const int cell = ii + gf.nx * (jj + gf.ny * kk);
+        const M rv = b[cell] - (dg[q] * x[cell] - mg_row_off<DIM, M>(gf, w[q], x, cell, ii, jj, kk));
+        acc += fl[q] ? rv : M(0);
     }
     bc[c] = acc;
-    xc[c] = M(0);
+    xc[c] = (first && ((i + j + k) & 1) == 0) ? acc * idq : M(0);
 }
 
 template <typename M>
 __global__ void k_mg_prolong(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
                              const M *__restrict__ xc, M *__restrict__ x) {
-    griddep_wait();
     CELL_IJK(gf);
+    const uint8_t f = inside ? fluid[c] : 0;
+    griddep_wait();
     if (!inside) return;
-    if (!fluid[c]) return;
-    x[c] += xc[(i / rx) + gc.nx * ((j / ry) + gc.ny * (k / rz))];
+    const M v = xc[(i / rx) + gc.nx * ((j / ry) + gc.ny * (k / rz))];
+    const M xo = x[c];
+    if (f) x[c] = xo + v;
 }
 
 static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ ff,
@@ -1139,16 +1185,20 @@ __global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, co
     ccoarse[f] = rr[A] == 2 ? M(0.5) * acc : acc;
 }
 
+// diagonal (sum of the face coefficients) and its reciprocal (0 on solid cells
+// and on fluid cells without coefficients)
 template <int DIM, typename M>
-__global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, M *__restrict__ diag) {
+__global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc, M *__restrict__ diag,
+                          M *__restrict__ idiag) {
     griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
-    if (!fluid[c]) { diag[c] = M(0); return; }
+    if (!fluid[c]) { diag[c] = M(0); idiag[c] = M(0); return; }
     M acc = M(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) acc += cc.a[a][flo(g, a, i, j, k)] + cc.a[a][fhi(g, a, i, j, k)];
     diag[c] = acc;
+    idiag[c] = acc > M(0) ? M(1) / acc : M(0);
 }
 
 // The V-cycle on the coarse levels in one CTA, with every level held in

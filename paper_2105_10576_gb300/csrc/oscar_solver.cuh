@@ -235,7 +235,8 @@ template <typename T> struct Impl {
                 }
             }
             L3 LL = launch3(L.g);
-            launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag), ++I.nlaunch;
+            launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag,
+                    (M *)L.idiag), ++I.nlaunch;
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -289,49 +290,53 @@ template <typename T> struct Impl {
         GridD g = to_dev(L.g);
         L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
         int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
-        launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (const M *)L.diag, x, b, colour),
+        launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour),
             ++I.nlaunch;
         prof_end(I, ps);
     }
 
     template <int DIM, int RX, int RY, int RZ>
-    static void rr_launch(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc) {
+    static void rr_launch(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc, int first) {
         L3 LC = launch3(C.g);
         launchk(k_mg_resid_restrict<DIM, M, RX, RY, RZ>, LC.grid, LC.block, 0, I.stream, to_dev(L.g), to_dev(C.g),
-                L.fluid, mg3(L), (const M *)L.diag, x, b, bc, xc);
+                L.fluid, mg3(L), (const M *)L.diag, x, b, bc, xc, (const M *)C.idiag, first);
         ++I.nlaunch;
     }
-    // fused residual + restriction, dispatched on the coarsening ratios
+    // fused residual + restriction (+ the coarse level's first colour-0 half
+    // sweep when first is set), dispatched on the coarsening ratios
     template <int DIM>
-    static void resid_restrict(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc) {
+    static void resid_restrict(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc,
+                               int first) {
         int code = (L.r[0] == 2) | ((L.r[1] == 2) << 1) | ((L.r[2] == 2) << 2);
         switch (code) {
-            case 1: rr_launch<DIM, 2, 1, 1>(I, L, C, x, b, bc, xc); break;
-            case 2: rr_launch<DIM, 1, 2, 1>(I, L, C, x, b, bc, xc); break;
-            case 3: rr_launch<DIM, 2, 2, 1>(I, L, C, x, b, bc, xc); break;
-            case 4: rr_launch<DIM, 1, 1, 2>(I, L, C, x, b, bc, xc); break;
-            case 5: rr_launch<DIM, 2, 1, 2>(I, L, C, x, b, bc, xc); break;
-            case 6: rr_launch<DIM, 1, 2, 2>(I, L, C, x, b, bc, xc); break;
-            case 7: rr_launch<DIM, 2, 2, 2>(I, L, C, x, b, bc, xc); break;
-            default: rr_launch<DIM, 1, 1, 1>(I, L, C, x, b, bc, xc); break;
+            case 1: rr_launch<DIM, 2, 1, 1>(I, L, C, x, b, bc, xc, first); break;
+            case 2: rr_launch<DIM, 1, 2, 1>(I, L, C, x, b, bc, xc, first); break;
+            case 3: rr_launch<DIM, 2, 2, 1>(I, L, C, x, b, bc, xc, first); break;
+            case 4: rr_launch<DIM, 1, 1, 2>(I, L, C, x, b, bc, xc, first); break;
+            case 5: rr_launch<DIM, 2, 1, 2>(I, L, C, x, b, bc, xc, first); break;
+            case 6: rr_launch<DIM, 1, 2, 2>(I, L, C, x, b, bc, xc, first); break;
+            case 7: rr_launch<DIM, 2, 2, 2>(I, L, C, x, b, bc, xc, first); break;
+            default: rr_launch<DIM, 1, 1, 1>(I, L, C, x, b, bc, xc, first); break;
         }
     }
 
     // z = V-cycle(r): pre-smoothing red-black, post-smoothing black-red
     // (symmetric, so a valid CG preconditioner); levels from lc0 down run in
-    // one CTA.
+    // one CTA. The first colour-0 half sweep of each level above the CTA is
+    // done by the kernel that produces its right-hand side (k_cg_init /
+    // k_cg_update for the finest level, the restriction for the others).
     template <int DIM>
     static int vcycle_d(Instance &I, V *r, V *z) {
-        if (cudaMemsetAsync(z, 0, (size_t)I.g.ncell * sizeof(V), I.stream) != cudaSuccess) return OSCAR_E_CUDA;
         for (int l = 0; l < I.lc0; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
             int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 0, x, b); smooth_level<DIM>(I, l, 1, x, b); }
-            GridD g = to_dev(L.g), gc = to_dev(C.g);
-            L3 LC = launch3(C.g);
+            for (int s = 0; s < nu; ++s) {
+                if (s > 0) smooth_level<DIM>(I, l, 0, x, b);
+                smooth_level<DIM>(I, l, 1, x, b);
+            }
             int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-            resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z));
+            resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z), l + 1 < I.lc0 ? 1 : 0);
             prof_end(I, ps);
         }
         CLevels<M> P;
@@ -356,12 +361,13 @@ template <typename T> struct Impl {
     // r = b - M q (FP64), ||b||^2, ||r||^2 into S_BB, S_RR, then the loop
     // decision of residual_control(mode)
     template <int DIM>
-    static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h) {
+    static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h,
+                           V *zero1, V *zero2) {
         GridD g = to_dev(I.g);
         L3 L = launch_rows(I.g, kRedBlocks);
-        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r, I.partials,
-                                                               I.red_stride, I.ticket, L.nblocks, I.scal, I.ctl,
-                                                               I.P.cg_rtol, mode, h), ++I.nlaunch;
+        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r,
+                (const V *)I.lev[0].idiag, (V *)I.cg_z, zero1, zero2, I.partials, I.red_stride, I.ticket, L.nblocks,
+                I.scal, I.ctl, I.P.cg_rtol, mode, h), ++I.nlaunch;
     }
 
     // one PCG iteration on M x = r with Krylov vectors z, p, Ap (type V)
@@ -379,8 +385,8 @@ template <typename T> struct Impl {
         launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap, I.partials,
                                                                     I.ticket, L.nblocks, I.scal), ++I.nlaunch;
         prof_end(I, ps);
-        launchk(k_cg_update<V>, kRedBlocks, BS, 0, I.stream, n, x, r, p, Ap, I.partials, I.ticket, I.scal, I.ctl,
-                                                        I.P.cg_maxit, target_slot, h), ++I.nlaunch;
+        launchk(k_cg_update<V>, L.grid, L.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag, z,
+                I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
         if (I.capturing) {
             I.n_cg_body = I.nlaunch - n0;
             I.cg_bodies_captured += 1;
@@ -394,27 +400,24 @@ template <typename T> struct Impl {
     template <int DIM>
     static int pcg_d(Instance &I, double *q, const double *b) {
         size_t nbytes = (size_t)I.g.ncell * sizeof(V);
+        (void)nbytes;
         if constexpr (sizeof(T) == sizeof(double)) {
-            if (cudaMemsetAsync(I.cg_p, 0, nbytes, I.stream) != cudaSuccess) return OSCAR_E_CUDA;
             cudaGraphConditionalHandle h;
             OSCAR_TRY(cond_handle(I, &h));
-            residual64<DIM>(I, q, b, 0, h);
+            residual64<DIM>(I, q, b, 0, h, (V *)I.cg_p, nullptr);
             return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h); });
         } else {
         cudaGraphConditionalHandle ho;
         OSCAR_TRY(cond_handle(I, &ho));
-        residual64<DIM>(I, q, b, 1, ho);
+        residual64<DIM>(I, q, b, 1, ho, (V *)I.cg_e, (V *)I.cg_p);
         return loop_while(I, ho, [&]() -> int {
             long long n0 = I.nlaunch, cg0 = I.cg_bodies_captured;
-            if (cudaMemsetAsync(I.cg_e, 0, nbytes, I.stream) != cudaSuccess ||
-                cudaMemsetAsync(I.cg_p, 0, nbytes, I.stream) != cudaSuccess)
-                return OSCAR_E_CUDA;
             cudaGraphConditionalHandle hi;
             OSCAR_TRY(cond_handle(I, &hi));
             launchk(k_inner_start, 1, 1, 0, I.stream, I.scal, I.ctl, hi), ++I.nlaunch;
             OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi); }));
             launchk(k_cg_correct<V>, kRedBlocks, BS, 0, I.stream, I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
-            residual64<DIM>(I, q, b, 2, ho);
+            residual64<DIM>(I, q, b, 2, ho, (V *)I.cg_e, (V *)I.cg_p);
             if (I.capturing) I.n_outer_body = (I.nlaunch - n0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
             OSCAR_LAUNCH_CHECK();
             return 0;
@@ -747,8 +750,8 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
         } else if (kid == OSCAR_KID_RESID0) {
             if (I.nlev > 1) {
                 Level &C = I.lev[1];
-                if (I.g.dim == 3) X::template resid_restrict<3>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x);
-                else X::template resid_restrict<2>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x);
+                if (I.g.dim == 3) X::template resid_restrict<3>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
+                else X::template resid_restrict<2>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
             }
         } else if (kid == OSCAR_KID_CG_APPLY) {
             if (I.g.dim == 3)
