@@ -65,8 +65,10 @@ def algorithmic_bytes(kid: int, c, es: int) -> float:
         nf += p["nx"] * p["ny"] * (p["nz"] + 1)
     if kid == 0:   # RB-GS half sweep: x (all) + b, 1/diag (half) + face coeffs (each face once) + x write (half)
         return n * (es + 0.5 * (2 * es) + 0.5 * es) + nf * es
-    if kid == 1:   # operator apply + dot: p read, Ap write, info (4), face coeffs once
-        return n * (es + es + 4) + nf * es
+    if kid == 1:   # operator apply + dot, face coeffs once, info (4)
+        if es == 8:   # FP64 path: p read, Ap written
+            return n * (2 * es + 4) + nf * es
+        return n * (5 * es + 4) + nf * es    # mixed: p = z + beta p, Ap = M z + beta Ap: z, p, Ap in; p, Ap out
     if kid == 2:   # HbyA: v, vold, hbya (d each), alpha, rA, G (d*d), info; phic faces once
         return n * (es * (3 * d + 2 + d * d) + 4) + nf * es
     if kid == 3:   # transport (3 kernels): low, ratio, update
@@ -110,7 +112,7 @@ def recorded_traffic(kid: int):
     return float(rec["traffic_bytes_per_launch"])
 
 
-KID_NAMES = {0: "k_mg_rbgs (finest level, half sweep)", 1: "k_cg_apply_dot", 2: "k_momentum_H",
+KID_NAMES = {0: "k_mg_rbgs (finest level, half sweep)", 1: "k_cg_pz_apply (mixed) / k_cg_apply_dot (FP64)", 2: "k_momentum_H",
              3: "k_transport_{low,ratio,update}", 4: "k_mg_residual (finest level)"}
 
 

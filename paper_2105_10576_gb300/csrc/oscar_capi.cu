@@ -145,6 +145,9 @@ static void carve(Instance &I, Carver &C) {
     I.cg_p = (double *)C.take(nc * sizeof(double));
     I.cg_Ap = (double *)C.take(nc * sizeof(double));
     I.cg_e = C.take(nc * es);
+    if (I.prec != OSCAR_FP64) {
+        for (int a = 0; a < 3; ++a) I.cf64[a] = (double *)C.take((size_t)I.g.nf[a] * sizeof(double));
+    }
     for (int a = 0; a < 3; ++a) {
         size_t nf = I.g.nf[a];
         I.nf[a] = C.take(nf * es);
@@ -161,6 +164,9 @@ static void carve(Instance &I, Carver &C) {
         for (int a = 0; a < 3; ++a) L.c[a] = C.take((size_t)L.g.nf[a] * es);
         L.diag = C.take(n * es);
         L.idiag = C.take(n * es);
+        if (l == 0 && I.prec == OSCAR_FP64) {
+            for (int a = 0; a < 3; ++a) I.cf64[a] = (double *)L.c[a];
+        }
         L.x = C.take(n * es);
         L.b = C.take(n * es);
         L.res = C.take(n * es);

@@ -87,6 +87,9 @@ struct Instance {
     double *u_sum[3], *p_vd, *p_cr;
     double *cg_b, *cg_r, *cg_z, *cg_p, *cg_Ap;   // Krylov vectors hold T on the mixed path
     void *cg_e;            // mixed path: correction of the outer defect-correction step (T)
+    // FP64 pressure operator: level-0 face coefficients in FP64 (the mixed
+    // path keeps copies; the FP64 path points at level 0's arrays)
+    double *cf64[3];
     // face fields (T)
     void *nf[3], *phi_vd[3], *phi_cr[3], *phic[3], *phis[3], *fst[3];
     // multigrid (level 0 coefficients are the pressure operator's)

@@ -590,7 +590,7 @@ __global__ void k_rA(GridD g, const uint32_t *__restrict__ info, const T *__rest
 template <int A, typename T>
 __global__ void k_face_coeffs(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ rA,
                               const T *__restrict__ kappa, const T *__restrict__ alpha, T sigma, int has_st,
-                              T *__restrict__ cf, T *__restrict__ fst) {
+                              T *__restrict__ cf, T *__restrict__ fst, double *__restrict__ cf64) {
     griddep_wait();
     FACE_IJK(g, A);
     int L, H;
@@ -605,6 +605,7 @@ __global__ void k_face_coeffs(GridD g, const uint32_t *__restrict__ info, const 
     }
     cf[f] = cc;
     fst[f] = fs;
+    if (cf64) cf64[f] = (double)cc;
 }
 
 // Gauss gradients of the velocity iterate: G[comp*3 + dir]
@@ -760,6 +761,30 @@ __device__ __forceinline__ V poisson_row(const GridD &g, uint32_t inf, int c, in
     return acc;
 }
 
+// The FP64 operator row, sum over the faces of w_f (q_c - q_nb) (interior)
+// and w_f q_c (outlet), from FP64 copies of the coefficients and with
+// explicit FMAs: FP64 instructions are scarce on GB300, and this takes two
+// per face. The differences are formed first, so a converged residual keeps
+// its accuracy when q carries a large common level.
+template <int DIM>
+__device__ __forceinline__ double poisson_row64(const GridD &g, uint32_t inf, int c, int i, int j, int k,
+                                                C3<double> w64, const double *__restrict__ q) {
+    const double qc = q[c];
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int off = noff(g, a);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int t = ftype(inf, a, s);
+            const int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
+            if (t == FT_INTERIOR) acc = fma(w64.a[a][f], qc - q[s ? c + off : c - off], acc);
+            else if (t == FT_OUTLET) acc = fma(w64.a[a][f], qc, acc);
+        }
+    }
+    return acc;
+}
+
 template <typename T>
 __device__ __forceinline__ double outlet_coeff(const GridD &g, uint32_t inf, int i, int j, int k, C3<T> cf) {
     return ftype(inf, 0, 1) == FT_OUTLET ? (double)cf.a[0][fhi(g, 0, i, j, k)] : 0.0;
@@ -768,7 +793,8 @@ __device__ __forceinline__ double outlet_coeff(const GridD &g, uint32_t inf, int
 // normalised residual (Section 3.2): res = sum |b - Mq|, nrm = sum |Mq - M qbar| + |b - M qbar|;
 // the finishing block stores E = res / (nrm + 1e-20)
 template <int DIM, typename T>
-__global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
+__global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, C3<double> w64,
+                          const double *__restrict__ q,
                           const double *__restrict__ b, double *__restrict__ scal, double inv_nf,
                           double *__restrict__ part, int stride, unsigned *__restrict__ ticket, int nb) {
     griddep_wait();
@@ -779,7 +805,7 @@ __global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
         if (i >= g.nx) continue;
         uint32_t inf = info[c];
         if (inf & INFO_FLUID) {
-            double Mq = poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
+            double Mq = poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
             double Mqbar = qbar * outlet_coeff<T>(g, inf, i, j, k, cf);
             res += fabs(b[c] - Mq);
             nrm += fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
@@ -908,7 +934,7 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 // colour 1), and the Krylov vectors named in zero1 / zero2 (may be null) are
 // cleared.
 template <int DIM, typename T, typename V>
-__global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const double *__restrict__ q,
+__global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double> w64, const double *__restrict__ q,
                           const double *__restrict__ b, V *__restrict__ r, const V *__restrict__ idiag0,
                           V *__restrict__ z, V *__restrict__ zero1, V *__restrict__ zero2, double *__restrict__ part,
                           int stride, unsigned *__restrict__ ticket, int nb, double *__restrict__ scal,
@@ -922,10 +948,10 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<T> cf, 
         V rv = V(0);
         if (inf & INFO_FLUID) {
             double bc = b[c];
-            double rc = bc - poisson_row<DIM, T, double>(g, inf, c, i, j, k, cf, q);
+            double rc = bc - poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
             rv = (V)rc;
-            bb += bc * bc;
-            rr += rc * rc;
+            bb = fma(bc, bc, bb);
+            rr = fma(rc, rc, rr);
         }
         r[c] = rv;
         z[c] = ((i + j + k) & 1) == 0 ? rv * idiag0[c] : V(0);
@@ -956,6 +982,40 @@ __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T>
             V y = poisson_row<DIM, T, V>(g, inf, c, i, j, k, cf, p);
             Ap[c] = y;
             accv += p[c] * y;
+        }
+    }
+    double acc = (double)accv, dummy = 0.0;
+    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, nb) && block_leader()) {
+        scal[S_PAP] = acc;
+        scal[S_ALPHA] = scal[S_RZ1] / acc;
+    }
+}
+
+// Mixed path: p = z + beta p and Ap = M z + beta Ap (the search direction
+// update folded into the operator apply: M p = M z + beta M p_old, so every
+// thread writes only its own cell), then p.Ap; beta = 0 starts afresh.
+template <int DIM, typename T, typename V>
+__global__ void k_cg_pz_apply(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const V *__restrict__ z,
+                              V *__restrict__ p, V *__restrict__ Ap, double *__restrict__ part,
+                              unsigned *__restrict__ ticket, int nb, double *__restrict__ scal) {
+    griddep_wait();
+    const V be = (V)scal[S_BETA];
+    const bool fresh = scal[S_BETA] == 0.0;
+    V accv = V(0);
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
+        uint32_t inf = info[c];
+        const V zc = z[c];
+        const V pn = fresh ? zc : zc + be * p[c];
+        p[c] = pn;
+        if (!(inf & INFO_FLUID)) {
+            Ap[c] = V(0);
+        } else {
+            const V y = poisson_row<DIM, T, V>(g, inf, c, i, j, k, cf, z);
+            const V an = fresh ? y : y + be * Ap[c];
+            Ap[c] = an;
+            accv += pn * an;
         }
     }
     double acc = (double)accv, dummy = 0.0;
@@ -1085,6 +1145,45 @@ __global__ void k_mg_rbgs(GridD g, MG3<M> cc, const M *__restrict__ idiag, M *__
     griddep_wait();
     if (!ok) return;
     x[cell] = (b[cell] + mg_row_off<DIM, M>(g, w, x, cell, i, j, k)) * id;
+}
+
+// The last half sweep of the finest level (colour 0) fused with r.z: the
+// thread of colour cell i also takes its row partner i ^ 1 (colour 1, final
+// already), so every cell is counted once; the finishing block sets
+// beta = (r.z)_new / (r.z)_old as k_cg_dot_rz does.
+template <int DIM, typename M>
+__global__ void k_mg_rbgs_dot(GridD g, MG3<M> cc, const M *__restrict__ idiag, M *__restrict__ x,
+                              const M *__restrict__ b, int colour, double *__restrict__ part,
+                              unsigned *__restrict__ ticket, double *__restrict__ scal) {
+    const int ti = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    const int i = 2 * ti + ((j + k + colour) & 1);
+    const bool ok = i < g.nx && j < g.ny;
+    const int cell = i + g.nx * (j + g.ny * k);
+    const int ip = i ^ 1;
+    const bool okp = ip < g.nx && j < g.ny;
+    const int cellp = ip + g.nx * (j + g.ny * k);
+    M w[2 * DIM], id = M(0);
+    if (ok) {
+        mg_row_coeffs<DIM, M>(g, cc, i, j, k, w);
+        id = idiag[cell];
+    }
+    griddep_wait();
+    M acc = M(0);
+    if (ok) {
+        const M bc = b[cell];
+        const M xn = (bc + mg_row_off<DIM, M>(g, w, x, cell, i, j, k)) * id;
+        x[cell] = xn;
+        acc = bc * xn;
+    }
+    if (okp) acc += b[cellp] * x[cellp];
+    double a64 = (double)acc, dummy = 0.0;
+    if (reduce_last(a64, dummy, 1, false, part, 0, ticket, gridDim.x * gridDim.y * gridDim.z) && block_leader()) {
+        double ro = scal[S_RZ0];
+        scal[S_RZ1] = a64;
+        scal[S_BETA] = ro != 0.0 ? a64 / ro : 0.0;
+    }
 }
 
 // coarse b = sum over children of the fine residual b - M x. With first set,

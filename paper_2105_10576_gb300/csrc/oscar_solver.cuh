@@ -157,6 +157,13 @@ template <typename T> struct Impl {
     using V = T;
     static T *tp(void *p) { return (T *)p; }
     static C3<T> c3(void *const *p) { C3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (const T *)p[a]; return r; }
+    static C3<double> w64(const Instance &I) {
+        C3<double> r;
+        for (int a = 0; a < 3; ++a) r.a[a] = I.cf64[a];
+        return r;
+    }
+    // FP64 copy of the level-0 coefficients of direction a (mixed path only)
+    static double *cf64_out(Instance &I, int a) { return sizeof(T) == sizeof(double) ? nullptr : I.cf64[a]; }
     static P3<T> p3(void *const *p) { P3<T> r; for (int a = 0; a < 3; ++a) r.a[a] = (T *)p[a]; return r; }
     static double *part(Instance &I, int slot) { return I.partials + (size_t)slot * I.red_stride; }
 
@@ -284,14 +291,19 @@ template <typename T> struct Impl {
     static M *lx(Instance &I, int l, V *z) { return l == 0 ? (M *)z : (M *)I.lev[l].x; }
     static M *lb(Instance &I, int l, V *r) { return l == 0 ? (M *)r : (M *)I.lev[l].b; }
 
+    // one half sweep; with_dot (finest level only) also forms r.z and beta
     template <int DIM>
-    static void smooth_level(Instance &I, int l, int colour, M *x, const M *b) {
+    static void smooth_level(Instance &I, int l, int colour, M *x, const M *b, bool with_dot = false) {
         Level &L = I.lev[l];
         GridD g = to_dev(L.g);
         L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
-        int ps = l == 0 ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
-        launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour),
-            ++I.nlaunch;
+        int ps = l == 0 && !with_dot ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
+        if (with_dot)
+            launchk(k_mg_rbgs_dot<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour,
+                    I.partials, I.ticket, I.scal), ++I.nlaunch;
+        else
+            launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour),
+                ++I.nlaunch;
         prof_end(I, ps);
     }
 
@@ -352,7 +364,10 @@ template <typename T> struct Impl {
             L3 LL = launch3(L.g);
             launchk(k_mg_prolong<M>, LL.grid, LL.block, 0, I.stream, g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
                                                                 (const M *)lx(I, l + 1, z), x), ++I.nlaunch;
-            for (int s = 0; s < nu; ++s) { smooth_level<DIM>(I, l, 1, x, b); smooth_level<DIM>(I, l, 0, x, b); }
+            for (int s = 0; s < nu; ++s) {
+                smooth_level<DIM>(I, l, 1, x, b);
+                smooth_level<DIM>(I, l, 0, x, b, l == 0 && s == nu - 1);   // the last one also forms r.z
+            }
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -365,7 +380,7 @@ template <typename T> struct Impl {
                            V *zero1, V *zero2) {
         GridD g = to_dev(I.g);
         L3 L = launch_rows(I.g, kRedBlocks);
-        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), q, b, (V *)I.cg_r,
+        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, w64(I), q, b, (V *)I.cg_r,
                 (const V *)I.lev[0].idiag, (V *)I.cg_z, zero1, zero2, I.partials, I.red_stride, I.ticket, L.nblocks,
                 I.scal, I.ctl, I.P.cg_rtol, mode, h), ++I.nlaunch;
     }
@@ -379,11 +394,17 @@ template <typename T> struct Impl {
         V *r = (V *)I.cg_r, *z = (V *)I.cg_z, *p = (V *)I.cg_p, *Ap = (V *)I.cg_Ap;
         long long n0 = I.nlaunch;
         OSCAR_TRY(vcycle_d<DIM>(I, r, z));
-        launchk(k_cg_dot_rz<V>, kRedBlocks, BS, 0, I.stream, n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
-        launchk(k_cg_pupdate<V>, kRedBlocks, BS, 0, I.stream, n, I.scal, z, p), ++I.nlaunch;
+        if (I.lc0 == 0)   // the whole V-cycle ran in the coarse CTA: r.z on its own
+            launchk(k_cg_dot_rz<V>, kRedBlocks, BS, 0, I.stream, n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
         int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
-        launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap, I.partials,
-                                                                    I.ticket, L.nblocks, I.scal), ++I.nlaunch;
+        if constexpr (sizeof(V) == sizeof(float)) {
+            launchk(k_cg_pz_apply<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), (const V *)z, p,
+                    Ap, I.partials, I.ticket, L.nblocks, I.scal), ++I.nlaunch;
+        } else {   // FP64 path: the search direction as written, M p applied directly
+            launchk(k_cg_pupdate<V>, kRedBlocks, BS, 0, I.stream, n, I.scal, z, p), ++I.nlaunch;
+            launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap,
+                    I.partials, I.ticket, L.nblocks, I.scal), ++I.nlaunch;
+        }
         prof_end(I, ps);
         launchk(k_cg_update<V>, L.grid, L.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag, z,
                 I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
@@ -438,12 +459,12 @@ template <typename T> struct Impl {
         T sig = (T)I.P.sigma;
         int st = has_st ? 1 : 0;
         launchk(k_face_coeffs<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
-                                                                    tp(cf[0]), tp(I.fst[0])), ++I.nlaunch;
+                                                                    tp(cf[0]), tp(I.fst[0]), cf64_out(I, 0)), ++I.nlaunch;
         launchk(k_face_coeffs<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
-                                                                    tp(cf[1]), tp(I.fst[1])), ++I.nlaunch;
+                                                                    tp(cf[1]), tp(I.fst[1]), cf64_out(I, 1)), ++I.nlaunch;
         if (DIM == 3)
             launchk(k_face_coeffs<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.rA), tp(I.kappa), al, sig, st,
-                                                                        tp(cf[2]), tp(I.fst[2])), ++I.nlaunch;
+                                                                        tp(cf[2]), tp(I.fst[2]), cf64_out(I, 2)), ++I.nlaunch;
         OSCAR_LAUNCH_CHECK();
         OSCAR_TRY(mg_coeffs_d<DIM>(I));
         P3<T> Gp0 = p3(&I.G[0]), Gp1 = p3(&I.G[3]), Gp2 = p3(&I.G[6]);
@@ -467,7 +488,8 @@ template <typename T> struct Impl {
                 launchk(k_sum_to<double>, kRedBlocks, BS, 0, I.stream, g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
                                                                   S_QSUM), ++I.nlaunch;
                 L3 LR = launch_rows(I.g, kRedBlocks);
-                launchk(k_normres<DIM, T>, LR.grid, LR.block, 0, I.stream, g, I.info, c3(cf), q, I.cg_b, I.scal,
+                launchk(k_normres<DIM, T>, LR.grid, LR.block, 0, I.stream, g, I.info, c3(cf), w64(I), q,
+                        I.cg_b, I.scal,
                                                                     1.0 / (double)I.n_fluid, I.partials, I.red_stride,
                                                                     I.ticket, LR.nblocks), ++I.nlaunch;
             }
@@ -753,15 +775,24 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
                 if (I.g.dim == 3) X::template resid_restrict<3>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
                 else X::template resid_restrict<2>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
             }
-        } else if (kid == OSCAR_KID_CG_APPLY) {
-            if (I.g.dim == 3)
-                launchk(k_cg_apply_dot<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks,
-                                                                          I.scal), ++I.nlaunch;
-            else
-                launchk(k_cg_apply_dot<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c), (const V *)I.cg_p,
-                                                                          (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks,
-                                                                          I.scal), ++I.nlaunch;
+        } else if (kid == OSCAR_KID_CG_APPLY) {   // the operator apply of the PCG iteration
+            if constexpr (sizeof(V) == sizeof(float)) {
+                if (I.g.dim == 3)
+                    launchk(k_cg_pz_apply<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
+                            (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal),
+                        ++I.nlaunch;
+                else
+                    launchk(k_cg_pz_apply<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
+                            (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal),
+                        ++I.nlaunch;
+            } else {
+                if (I.g.dim == 3)
+                    launchk(k_cg_apply_dot<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
+                            (const V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal), ++I.nlaunch;
+                else
+                    launchk(k_cg_apply_dot<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
+                            (const V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal), ++I.nlaunch;
+            }
         } else if (kid == OSCAR_KID_MOMENTUM) {
             C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
             if (I.g.dim == 3)
