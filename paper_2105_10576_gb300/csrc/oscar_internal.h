@@ -18,7 +18,7 @@ constexpr double kSyncTimeoutSec = 600.0;
 // Scalar slots in the device scalar array (double).
 enum Slot {
     S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_TARGET, S_E, S_DU, S_TEST,
-    S_ITARGET, S_ALPHA, S_BETA, S_TMP, S_COUNT
+    S_ITARGET, S_ALPHA, S_BETA, S_ALPHA_F, S_BETA_F, S_TMP, S_COUNT
 };
 
 // Integer control words on the device (relaxation and PCG loop state).

@@ -34,6 +34,8 @@ constexpr uint32_t INFO_FLUID = 1u << 31;
 constexpr int BS = 256;
 constexpr int kCtaCells = 1024;      // levels at or below this size run in one CTA
 constexpr int kMaxCL = 16;
+constexpr int kApplyRows = 2;    // rows per thread of k_cg_pz_apply
+constexpr int kUpdateRows = 4;   // rows per thread of k_cg_update
 
 // Programmatic dependent launch: wait until the preceding kernel has
 // completed and its writes are visible, then let the next kernel's CTAs be
@@ -119,6 +121,18 @@ inline L3 launch_rows(const GridH &g, int target) {
 
 #define BLOCK_ID() ((int)(blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)))
 
+// Blocks of launch3's shape over (x, rows) where each thread takes RPT rows,
+// row = blockIdx.y * blockDim.y * RPT + threadIdx.y + u * blockDim.y, u < RPT
+// (the kernels unroll u so that the loads of all their rows are in flight
+// together)
+inline L3 launch_rpt(const GridH &g, int rpt) {
+    L3 l = launch3(g.nx, g.ny * g.nz, 1);
+    const int by = (int)l.block.y, rows = g.ny * g.nz;
+    l.grid = dim3(l.grid.x, (rows + by * rpt - 1) / (by * rpt), 1);
+    l.nblocks = (int)(l.grid.x * l.grid.y);
+    return l;
+}
+
 // Row loop of the stencil reductions (launch_rows): the thread at x = i takes
 // every (gridDim.y * blockDim.y)-th row, row = j + ny k, so that a thread sums
 // several cells before the block reduction.
@@ -201,6 +215,57 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max) {
 }
 __device__ __forceinline__ double block_sum(double v) { return block_reduce(v, false); }
 __device__ __forceinline__ double block_max(double v) { return block_reduce(v, true); }
+// Compensated block sum of FP32 values: the (sum, rounding error) pair is
+// carried through the shuffle tree with error-free TwoSum steps (Knuth), so
+// the block total matches the FP64 sum of the thread values to about 2^-44
+// relative, with FP32 instructions only; returned in FP64 (valid in thread 0).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void warp_sum_pair(float &s, float &e) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_down_sync(0xffffffffu, s, o), eo = __shfl_down_sync(0xffffffffu, e, o);
+        float t, err;
+        two_sum(s, so, t, err);
+        s = t;
+        e += eo + err;
+    }
+}
+__device__ __forceinline__ double block_sum_f(float v) {
+    __shared__ float shs[32], she[32];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    const int w = t >> 5, l = t & 31, nw = nt >> 5;
+    float s = v, e = 0.f;
+    warp_sum_pair(s, e);
+    __syncthreads();
+    if (l == 0) { shs[w] = s; she[w] = e; }
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        s = l < nw ? shs[l] : 0.f;
+        e = l < nw ? she[l] : 0.f;
+        warp_sum_pair(s, e);
+        if (l == 0) r = (double)s + (double)e;
+    }
+    return r;
+}
+
+// CG scalars: the finishing block stores alpha / beta in FP64 and an FP32
+// copy in the slot's f-twin, so FP32 kernels read them without FP64 work
+__device__ __forceinline__ void put_scalar(double *scal, int slot, int fslot, double v) {
+    scal[slot] = v;
+    *reinterpret_cast<float *>(scal + fslot) = (float)v;
+}
+template <typename V> __device__ __forceinline__ V get_scalar(const double *scal, int slot, int fslot);
+template <> __device__ __forceinline__ float get_scalar<float>(const double *scal, int, int fslot) {
+    return *reinterpret_cast<const float *>(scal + fslot);
+}
+template <> __device__ __forceinline__ double get_scalar<double>(const double *scal, int slot, int) {
+    return scal[slot];
+}
+
 __device__ __forceinline__ bool block_leader() { return threadIdx.x == 0 && threadIdx.y == 0; }
 
 // Single-pass reduction: every block stores its partial(s); the block that
@@ -242,6 +307,43 @@ __device__ __forceinline__ bool reduce_last(double &v0, double &v1, int nv, bool
     v0 = tot_s[0];
     v1 = tot_s[1];
     return true;
+}
+
+// reduce_last for one sum of FP32 thread values (compensated block sums,
+// FP64 across blocks); the total is returned in v (all threads of the last
+// block). An FP64 value goes through reduce_last.
+__device__ __forceinline__ bool reduce_last_sum(float v, double &out, double *__restrict__ part,
+                                                unsigned *__restrict__ ticket, int nb) {
+    const double bs = block_sum_f(v);
+    __shared__ int last_f;
+    __shared__ double tot_f;
+    if (block_leader()) {
+        part[BLOCK_ID()] = bs;
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last_f = (t == (unsigned)(nb - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last_f) return false;
+    __threadfence();
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    double s0 = 0.0;
+    for (int q = tid; q < nb; q += nt) s0 += __ldcg(part + q);
+    s0 = block_sum(s0);
+    if (block_leader()) {
+        tot_f = s0;
+        *ticket = 0u;
+    }
+    __syncthreads();
+    out = tot_f;
+    return true;
+}
+__device__ __forceinline__ bool reduce_last_sum(double v, double &out, double *__restrict__ part,
+                                                unsigned *__restrict__ ticket, int nb) {
+    double dummy = 0.0;
+    const bool last = reduce_last(v, dummy, 1, false, part, 0, ticket, nb);
+    out = v;
+    return last;
 }
 
 // Loop-control decisions taken by the finishing block: each writes
@@ -984,69 +1086,143 @@ __global__ void k_cg_apply_dot(GridD g, const uint32_t *__restrict__ info, C3<T>
             accv += p[c] * y;
         }
     }
-    double acc = (double)accv, dummy = 0.0;
-    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, nb) && block_leader()) {
+    double acc;
+    if (reduce_last_sum(accv, acc, part, ticket, nb) && block_leader()) {
         scal[S_PAP] = acc;
-        scal[S_ALPHA] = scal[S_RZ1] / acc;
+        put_scalar(scal, S_ALPHA, S_ALPHA_F, scal[S_RZ1] / acc);
     }
 }
 
 // Mixed path: p = z + beta p and Ap = M z + beta Ap (the search direction
 // update folded into the operator apply: M p = M z + beta M p_old, so every
-// thread writes only its own cell), then p.Ap; beta = 0 starts afresh.
-template <int DIM, typename T, typename V>
+// thread writes only its own cell), then p.Ap; beta = 0 starts afresh. Each
+// thread takes RPT rows (launch_rpt); the cell flags and face coefficients,
+// fixed during a solve, are loaded before the grid dependency wait, the
+// vectors after it, all rows at once.
+template <int DIM, typename T, typename V, int RPT>
 __global__ void k_cg_pz_apply(GridD g, const uint32_t *__restrict__ info, C3<T> cf, const V *__restrict__ z,
                               V *__restrict__ p, V *__restrict__ Ap, double *__restrict__ part,
                               unsigned *__restrict__ ticket, int nb, double *__restrict__ scal) {
-    griddep_wait();
-    const V be = (V)scal[S_BETA];
-    const bool fresh = scal[S_BETA] == 0.0;
-    V accv = V(0);
-    ROW_LOOP(g) {
-        ROW_CELL(g);
-        if (i >= g.nx) continue;
-        uint32_t inf = info[c];
-        const V zc = z[c];
-        const V pn = fresh ? zc : zc + be * p[c];
-        p[c] = pn;
-        if (!(inf & INFO_FLUID)) {
-            Ap[c] = V(0);
-        } else {
-            const V y = poisson_row<DIM, T, V>(g, inf, c, i, j, k, cf, z);
-            const V an = fresh ? y : y + be * Ap[c];
-            Ap[c] = an;
-            accv += pn * an;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nrow = g.ny * g.nz;
+    const int row0 = blockIdx.y * blockDim.y * RPT + threadIdx.y;
+    uint32_t inf[RPT];
+    T w[RPT][2 * DIM];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        inf[u] = 0;
+        if (i < g.nx && row < nrow) {
+            const int k = row / g.ny, j = row - k * g.ny, c = i + g.nx * row;
+            inf[u] = info[c];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                w[u][2 * a] = cf.a[a][flo(g, a, i, j, k)];
+                w[u][2 * a + 1] = cf.a[a][fhi(g, a, i, j, k)];
+            }
         }
     }
-    double acc = (double)accv, dummy = 0.0;
-    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, nb) && block_leader()) {
+    griddep_wait();
+    const V be = get_scalar<V>(scal, S_BETA, S_BETA_F);
+    const bool fresh = be == V(0);
+    V zc[RPT], zn[RPT][2 * DIM], po[RPT], ao[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        if (i < g.nx && row < nrow) {
+            const int k = row / g.ny, j = row - k * g.ny, c = i + g.nx * row;
+            const int ijk[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz};
+            zc[u] = z[c];
+            po[u] = p[c];
+            ao[u] = Ap[c];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const int off = noff(g, a);
+                zn[u][2 * a] = ijk[a] > 0 ? z[c - off] : V(0);
+                zn[u][2 * a + 1] = ijk[a] < n[a] - 1 ? z[c + off] : V(0);
+            }
+        }
+    }
+    V accv = V(0);
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        if (i >= g.nx || row >= nrow) continue;
+        const int c = i + g.nx * row;
+        const V pn = fresh ? zc[u] : zc[u] + be * po[u];
+        p[c] = pn;
+        if (!(inf[u] & INFO_FLUID)) {
+            Ap[c] = V(0);
+            continue;
+        }
+        V y = V(0);   // same terms and order as poisson_row
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2) {
+                const int t = ftype(inf[u], a, s2);
+                if (t == FT_INTERIOR) y += (V)w[u][2 * a + s2] * (zc[u] - zn[u][2 * a + s2]);
+                else if (t == FT_OUTLET) y += (V)w[u][2 * a + s2] * zc[u];
+            }
+        }
+        const V an = fresh ? y : y + be * ao[u];
+        Ap[c] = an;
+        accv += pn * an;
+    }
+    double acc;
+    if (reduce_last_sum(accv, acc, part, ticket, nb) && block_leader()) {
         scal[S_PAP] = acc;
-        scal[S_ALPHA] = scal[S_RZ1] / acc;
+        put_scalar(scal, S_ALPHA, S_ALPHA_F, scal[S_RZ1] / acc);
     }
 }
 
 // x += alpha p, r -= alpha Ap, and z = the first colour-0 half sweep of the
 // next V-cycle (as in k_cg_init); the finishing block tests ||r|| against
-// scal[target_slot] and decides whether the PCG loop continues
-template <typename V>
+// scal[target_slot] and decides whether the PCG loop continues. RPT rows per
+// thread (launch_rpt), loaded together.
+template <typename V, int RPT>
 __global__ void k_cg_update(GridD g, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
                             const V *__restrict__ Ap, const V *__restrict__ idiag0, V *__restrict__ z,
                             double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
                             int *__restrict__ ctl, int maxit, int target_slot, cudaGraphConditionalHandle h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nrow = g.ny * g.nz;
+    const int row0 = blockIdx.y * blockDim.y * RPT + threadIdx.y;
+    V id[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        id[u] = (i < g.nx && row < nrow) ? idiag0[i + g.nx * row] : V(0);
+    }
     griddep_wait();
-    const V al = (V)scal[S_ALPHA];
+    const V al = get_scalar<V>(scal, S_ALPHA, S_ALPHA_F);
+    V xo[RPT], ro[RPT], pc[RPT], ac[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        if (i < g.nx && row < nrow) {
+            const int c = i + g.nx * row;
+            xo[u] = x[c];
+            ro[u] = r[c];
+            pc[u] = p[c];
+            ac[u] = Ap[c];
+        }
+    }
     V accv = V(0);
-    ROW_LOOP(g) {
-        ROW_CELL(g);
-        if (i >= g.nx) continue;
-        x[c] += al * p[c];
-        V rc = r[c] - al * Ap[c];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int row = row0 + u * blockDim.y;
+        if (i >= g.nx || row >= nrow) continue;
+        const int c = i + g.nx * row;
+        const int k = row / g.ny, j = row - k * g.ny;
+        x[c] = xo[u] + al * pc[u];
+        const V rc = ro[u] - al * ac[u];
         r[c] = rc;
-        z[c] = ((i + j + k) & 1) == 0 ? rc * idiag0[c] : V(0);
+        z[c] = ((i + j + k) & 1) == 0 ? rc * id[u] : V(0);
         accv += rc * rc;
     }
-    double acc = (double)accv, dummy = 0.0;
-    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x * gridDim.y) && block_leader()) {
+    double acc;
+    if (reduce_last_sum(accv, acc, part, ticket, gridDim.x * gridDim.y) && block_leader()) {
         scal[S_RR] = acc;
         int it = ++ctl[C_IT];
         ctl[C_ITSUM] += 1;
@@ -1067,11 +1243,11 @@ __global__ void k_cg_dot_rz(int n, const V *__restrict__ x, const V *__restrict_
     griddep_wait();
     V accv = V(0);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) accv += x[c] * y[c];
-    double acc = (double)accv, dummy = 0.0;
-    if (reduce_last(acc, dummy, 1, false, part, 0, ticket, gridDim.x) && block_leader()) {
+    double acc;
+    if (reduce_last_sum(accv, acc, part, ticket, gridDim.x) && block_leader()) {
         double ro = scal[S_RZ0];
         scal[S_RZ1] = acc;
-        scal[S_BETA] = ro != 0.0 ? acc / ro : 0.0;
+        put_scalar(scal, S_BETA, S_BETA_F, ro != 0.0 ? acc / ro : 0.0);
     }
 }
 
@@ -1079,7 +1255,7 @@ __global__ void k_cg_dot_rz(int n, const V *__restrict__ x, const V *__restrict_
 template <typename V>
 __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__restrict__ z, V *__restrict__ p) {
     griddep_wait();
-    const V be = (V)scal[S_BETA];
+    const V be = get_scalar<V>(scal, S_BETA, S_BETA_F);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
 }
 
@@ -1178,11 +1354,11 @@ __global__ void k_mg_rbgs_dot(GridD g, MG3<M> cc, const M *__restrict__ idiag, M
         acc = bc * xn;
     }
     if (okp) acc += b[cellp] * x[cellp];
-    double a64 = (double)acc, dummy = 0.0;
-    if (reduce_last(a64, dummy, 1, false, part, 0, ticket, gridDim.x * gridDim.y * gridDim.z) && block_leader()) {
+    double a64;
+    if (reduce_last_sum(acc, a64, part, ticket, gridDim.x * gridDim.y * gridDim.z) && block_leader()) {
         double ro = scal[S_RZ0];
         scal[S_RZ1] = a64;
-        scal[S_BETA] = ro != 0.0 ? a64 / ro : 0.0;
+        put_scalar(scal, S_BETA, S_BETA_F, ro != 0.0 ? a64 / ro : 0.0);
     }
 }
 

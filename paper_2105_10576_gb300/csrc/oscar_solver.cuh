@@ -398,16 +398,18 @@ template <typename T> struct Impl {
             launchk(k_cg_dot_rz<V>, kRedBlocks, BS, 0, I.stream, n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
         int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
         if constexpr (sizeof(V) == sizeof(float)) {
-            launchk(k_cg_pz_apply<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), (const V *)z, p,
-                    Ap, I.partials, I.ticket, L.nblocks, I.scal), ++I.nlaunch;
+            L3 LA = launch_rpt(I.g, kApplyRows);
+            launchk(k_cg_pz_apply<DIM, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info, c3(I.lev[0].c),
+                    (const V *)z, p, Ap, I.partials, I.ticket, LA.nblocks, I.scal), ++I.nlaunch;
         } else {   // FP64 path: the search direction as written, M p applied directly
             launchk(k_cg_pupdate<V>, kRedBlocks, BS, 0, I.stream, n, I.scal, z, p), ++I.nlaunch;
             launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap,
                     I.partials, I.ticket, L.nblocks, I.scal), ++I.nlaunch;
         }
         prof_end(I, ps);
-        launchk(k_cg_update<V>, L.grid, L.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag, z,
-                I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
+        L3 LU = launch_rpt(I.g, kUpdateRows);
+        launchk(k_cg_update<V, kUpdateRows>, LU.grid, LU.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag,
+                z, I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
         if (I.capturing) {
             I.n_cg_body = I.nlaunch - n0;
             I.cg_bodies_captured += 1;
@@ -759,7 +761,7 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OSCAR_E_CUDA;
     GridD g = to_dev(I.g);
-    L3 L = launch3(I.g), LR = launch_rows(I.g, kRedBlocks);
+    L3 L = launch3(I.g), LR = launch_rows(I.g, kRedBlocks), LA = launch_rpt(I.g, kApplyRows);
     double dt = I.last_dt > 0 ? I.last_dt : 1e-7;
     Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
     Level &L0 = I.lev[0];
@@ -778,12 +780,14 @@ template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int re
         } else if (kid == OSCAR_KID_CG_APPLY) {   // the operator apply of the PCG iteration
             if constexpr (sizeof(V) == sizeof(float)) {
                 if (I.g.dim == 3)
-                    launchk(k_cg_pz_apply<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
-                            (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal),
+                    launchk(k_cg_pz_apply<3, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info,
+                            X::c3(I.lev[0].c), (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket,
+                            LA.nblocks, I.scal),
                         ++I.nlaunch;
                 else
-                    launchk(k_cg_pz_apply<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
-                            (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal),
+                    launchk(k_cg_pz_apply<2, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info,
+                            X::c3(I.lev[0].c), (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket,
+                            LA.nblocks, I.scal),
                         ++I.nlaunch;
             } else {
                 if (I.g.dim == 3)
