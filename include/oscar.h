@@ -98,6 +98,8 @@ typedef struct {
     long long cell_updates;   /* fluid cells x (drag + relaxation + standard steps) since creation */
     size_t device_bytes;      /* device memory held by the handle */
     long long kernel_launches; /* CUDA kernels launched by this handle since creation */
+    int mg_first_cta_level;   /* first multigrid level held in one CTA's shared memory */
+    int mg_first_cluster_level; /* first level of the thread-block-cluster kernel, -1 when unused */
 } oscar_stats_t;
 
 typedef struct oscar_instance *oscar_handle;

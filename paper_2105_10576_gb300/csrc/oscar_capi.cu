@@ -423,6 +423,8 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out) {
     out->cell_updates = I.cell_updates;
     out->device_bytes = I.arena_bytes;
     out->kernel_launches = I.nexec;
+    out->mg_first_cta_level = I.lc0;
+    out->mg_first_cluster_level = I.lA;
     return 0;
 }
 

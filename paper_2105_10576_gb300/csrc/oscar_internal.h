@@ -100,6 +100,8 @@ struct Instance {
     int red_stride;        // partials per slot: max(kRedBlocks, blocks of a cell launch)
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     size_t cta_smem;       // shared memory of the coarse kernel
+    int lA;                // first level of the cluster kernel (mixed path), -1 when it is not used
+    size_t cl_smem;        // shared memory per CTA of the cluster kernel
     unsigned *ticket;      // block counter of the single-pass reductions (0 between kernels)
     double *scal;          // S_COUNT device scalars
     double *scal_host;     // pinned mirror

@@ -52,6 +52,29 @@ inline void launchk(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, 
     cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// one cluster of kClusterCtas CTAs of kCtaThreads threads, with programmatic
+// dependent launch like launchk
+template <typename... KArgs, typename... Args>
+inline void launch_cluster(void (*kern)(KArgs...), size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(kClusterCtas);
+    cfg.blockDim = dim3(kCtaThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = kClusterCtas;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+
 
 // ---------------------------------------------------------------------------
 // control kernels (one thread). The other loop decisions are taken by the
@@ -251,12 +274,12 @@ template <typename T> struct Impl {
 
     // levels l0.. of the single-CTA coarse kernel with their shared-memory
     // layout; returns the bytes of shared memory they need
-    static size_t cta_levels(Instance &I, CLevels<M> &P, int l0) {
+    static size_t cta_levels(Instance &I, CLevels<M> &P, int l0, size_t base = 0) {
         P.n = I.nlev - l0;
         P.nu = I.mg_nu_c;
         P.nu_top = l0 == 0 ? I.mg_nu : I.mg_nu_c;
         P.coarse_sweeps = I.mg_coarse_sweeps;
-        size_t off = 0;
+        size_t off = base;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
         size_t nmax = 0;
         for (int q = 0; q < P.n && q < kMaxCL; ++q) {
@@ -285,6 +308,45 @@ template <typename T> struct Impl {
         }
         P.ors = take(nmax * sizeof(M));
         return P.n > kMaxCL ? (size_t)-1 : off;
+    }
+
+    // Levels lA .. lc0-1 as x-slabs of the cluster kernel, the levels below on
+    // rank 0; returns the shared memory per CTA, or (size_t)-1 when a level
+    // does not split into kClusterCtas slabs aligned with its coarsening.
+    static size_t cluster_levels(Instance &I, SLevels<M> &P, int lA) {
+        P.n = I.lc0 - lA;
+        if (lA < 1 || P.n < 1 || P.n > kMaxSL) return (size_t)-1;
+        P.nu = I.mg_nu_c;
+        P.nu_top = I.mg_nu_c;
+        size_t off = 0, nmax = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
+        for (int q = 0; q < P.n; ++q) {
+            Level &L = I.lev[lA + q];
+            SLevel<M> &S = P.L[q];
+            if (L.g.nx % kClusterCtas != 0) return (size_t)-1;
+            const int sx = L.g.nx / kClusterCtas;
+            if (sx % L.r[0] != 0) return (size_t)-1;
+            S.g = to_dev(L.g);
+            S.sx = sx;
+            for (int a = 0; a < 3; ++a) { S.c[a] = (const M *)L.c[a]; S.r[a] = L.r[a]; }
+            S.idiag = (const M *)L.idiag;
+            S.rsx = 1.0f / (float)sx;
+            S.rsx1 = 1.0f / (float)(sx + 1);
+            S.rny = 1.0f / (float)L.g.ny;
+            S.rny1 = 1.0f / (float)(L.g.ny + 1);
+            S.rhx = 1.0f / (float)((sx + 1) / 2);
+            const size_t n = (size_t)sx * L.g.ny * L.g.nz;
+            nmax = n > nmax ? n : nmax;
+            S.ox = take(n * sizeof(M));
+            S.ob = take(n * sizeof(M));
+            S.oi = take(n * sizeof(M));
+            S.oc[0] = take((size_t)(sx + 1) * L.g.ny * L.g.nz * sizeof(M));
+            S.oc[1] = take((size_t)sx * (L.g.ny + 1) * L.g.nz * sizeof(M));
+            S.oc[2] = take(L.g.dim == 3 ? (size_t)sx * L.g.ny * (L.g.nz + 1) * sizeof(M) : 0);
+        }
+        P.ors = take(nmax * sizeof(M));
+        size_t tot = cta_levels(I, P.C, I.lc0, off);
+        return P.C.n > kMaxCL ? (size_t)-1 : tot;
     }
 
     // x / b of level l (level 0 works in place on the Krylov vectors z / r)
@@ -339,7 +401,8 @@ template <typename T> struct Impl {
     // k_cg_update for the finest level, the restriction for the others).
     template <int DIM>
     static int vcycle_d(Instance &I, V *r, V *z) {
-        for (int l = 0; l < I.lc0; ++l) {
+        const int lk = I.lA > 0 ? I.lA : I.lc0;   // first level not worked by per-level kernels
+        for (int l = 0; l < lk; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
             int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
@@ -348,15 +411,25 @@ template <typename T> struct Impl {
                 smooth_level<DIM>(I, l, 1, x, b);
             }
             int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
-            resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z), l + 1 < I.lc0 ? 1 : 0);
+            resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z), l + 1 < lk ? 1 : 0);
             prof_end(I, ps);
         }
-        CLevels<M> P;
-        cta_levels(I, P, I.lc0);
-        P.b_top = lb(I, I.lc0, r);
-        P.x_top = lx(I, I.lc0, z);
-        launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P), ++I.nlaunch;
-        for (int l = I.lc0 - 1; l >= 0; --l) {
+        if (I.lA > 0) {
+            if constexpr (sizeof(M) == sizeof(float)) {
+                SLevels<M> P;
+                cluster_levels(I, P, I.lA);
+                P.b_top = lb(I, I.lA, r);
+                P.x_top = lx(I, I.lA, z);
+                launch_cluster(k_mg_cluster<DIM, M>, I.cl_smem, I.stream, P), ++I.nlaunch;
+            }
+        } else {
+            CLevels<M> P;
+            cta_levels(I, P, I.lc0);
+            P.b_top = lb(I, I.lc0, r);
+            P.x_top = lx(I, I.lc0, z);
+            launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P), ++I.nlaunch;
+        }
+        for (int l = lk - 1; l >= 0; --l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
             int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
@@ -727,6 +800,49 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                                  : cudaFuncSetAttribute(k_mg_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)I.cta_smem);
     if (e != cudaSuccess) return OSCAR_E_CUDA;
+    // mixed path, opt-in (OSCAR_CLUSTER=1): the levels between the per-level
+    // kernels and the coarse CTA go to the cluster kernel when they split
+    // into aligned slabs and fit. On the 3D constriction it measured slower
+    // than the per-level launches (cluster barriers plus distributed-shared-
+    // memory halo reads cost about as much per phase as a dependent launch,
+    // and the per-launch reload of the slabs is not amortised).
+    I.lA = -1;
+    I.cl_smem = 0;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const char *ec = getenv("OSCAR_CLUSTER");
+        const bool want = ec && atoi(ec) == 1;
+        SLevels<T> S;
+        for (int lA = 1; want && lA < I.lc0; ++lA) {
+            size_t sm = Impl<T>::cluster_levels(I, S, lA);
+            if (sm == (size_t)-1 || sm > budget) continue;
+            void (*kern)(SLevels<T>) = I.g.dim == 3 ? k_mg_cluster<3, T> : k_mg_cluster<2, T>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            cudaLaunchConfig_t cfg;
+            memset(&cfg, 0, sizeof(cfg));
+            cfg.gridDim = dim3(kClusterCtas);
+            cfg.blockDim = dim3(kCtaThreads);
+            cfg.dynamicSmemBytes = sm;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = kClusterCtas;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            if (cudaOccupancyMaxActiveClusters(&ncl, (void *)kern, &cfg) != cudaSuccess || ncl < 1) {
+                cudaGetLastError();
+                break;
+            }
+            I.lA = lA;
+            I.cl_smem = sm;
+            break;
+        }
+    }
     int rc = Impl<T>::interface_(I, I.alpha);
     I.nexec += I.nlaunch - l0;
     return rc;
