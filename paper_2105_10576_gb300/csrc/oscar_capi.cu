@@ -145,6 +145,7 @@ static void carve(Instance &I, Carver &C) {
     I.cg_p = (double *)C.take(nc * sizeof(double));
     I.cg_Ap = (double *)C.take(nc * sizeof(double));
     I.cg_e = C.take(nc * es);
+    I.cg_r64 = I.prec != OSCAR_FP64 ? (double *)C.take(nc * sizeof(double)) : nullptr;
     if (I.prec != OSCAR_FP64) {
         for (int a = 0; a < 3; ++a) I.cf64[a] = (double *)C.take((size_t)I.g.nf[a] * sizeof(double));
     }

@@ -87,6 +87,7 @@ struct Instance {
     double *u_sum[3], *p_vd, *p_cr;
     double *cg_b, *cg_r, *cg_z, *cg_p, *cg_Ap;   // Krylov vectors hold T on the mixed path
     void *cg_e;            // mixed path: correction of the outer defect-correction step (T)
+    double *cg_r64;        // mixed path: FP64 residual b - M q of the outer defect correction
     // FP64 pressure operator: level-0 face coefficients in FP64 (the mixed
     // path keeps copies; the FP64 path points at level 0's arrays)
     double *cf64[3];

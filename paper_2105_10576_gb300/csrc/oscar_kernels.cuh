@@ -1035,11 +1035,12 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 // The kernel also starts the first V-cycle: z receives the colour-0 half
 // sweep of the finest level from z = 0 (z = r / diagonal on colour 0, 0 on
 // colour 1), and the Krylov vectors named in zero1 / zero2 (may be null) are
-// cleared.
+// cleared. r64 (may be null) receives r in FP64.
 template <int DIM, typename T, typename V>
 __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double> w64, const double *__restrict__ q,
-                          const double *__restrict__ b, V *__restrict__ r, const V *__restrict__ idiag0,
-                          V *__restrict__ z, V *__restrict__ zero1, V *__restrict__ zero2, double *__restrict__ part,
+                          const double *__restrict__ b, V *__restrict__ r, double *__restrict__ r64,
+                          const V *__restrict__ idiag0, V *__restrict__ z, V *__restrict__ zero1,
+                          V *__restrict__ zero2, double *__restrict__ part,
                           int stride, unsigned *__restrict__ ticket, int nb, double *__restrict__ scal,
                           int *__restrict__ ctl, double rtol, int mode, cudaGraphConditionalHandle h) {
     griddep_wait();
@@ -1049,14 +1050,16 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double>
         if (i >= g.nx) continue;
         uint32_t inf = info[c];
         V rv = V(0);
+        double rc = 0.0;
         if (inf & INFO_FLUID) {
             double bc = b[c];
-            double rc = bc - poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
+            rc = bc - poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
             rv = (V)rc;
             bb = fma(bc, bc, bb);
             rr = fma(rc, rc, rr);
         }
         r[c] = rv;
+        if (r64) r64[c] = rc;
         z[c] = ((i + j + k) & 1) == 0 ? rv * idiag0[c] : V(0);
         if (zero1) zero1[c] = V(0);
         if (zero2) zero2[c] = V(0);
@@ -1180,12 +1183,14 @@ __global__ void k_cg_pz_apply(GridD g, const uint32_t *__restrict__ info, C3<T> 
 // x += alpha p, r -= alpha Ap, and z = the first colour-0 half sweep of the
 // next V-cycle (as in k_cg_init); the finishing block tests ||r|| against
 // scal[target_slot] and decides whether the PCG loop continues. RPT rows per
-// thread (launch_rpt), loaded together.
+// thread (launch_rpt), loaded together. xfresh: x starts from 0 in the first
+// iteration (x is not read then), so it needs no clearing beforehand.
 template <typename V, int RPT>
 __global__ void k_cg_update(GridD g, V *__restrict__ x, V *__restrict__ r, const V *__restrict__ p,
                             const V *__restrict__ Ap, const V *__restrict__ idiag0, V *__restrict__ z,
                             double *__restrict__ part, unsigned *__restrict__ ticket, double *__restrict__ scal,
-                            int *__restrict__ ctl, int maxit, int target_slot, cudaGraphConditionalHandle h) {
+                            int *__restrict__ ctl, int maxit, int target_slot, int xfresh,
+                            cudaGraphConditionalHandle h) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nrow = g.ny * g.nz;
     const int row0 = blockIdx.y * blockDim.y * RPT + threadIdx.y;
@@ -1197,13 +1202,16 @@ __global__ void k_cg_update(GridD g, V *__restrict__ x, V *__restrict__ r, const
     }
     griddep_wait();
     const V al = get_scalar<V>(scal, S_ALPHA, S_ALPHA_F);
+    // with xfresh, the first iteration of a solve (iteration counter still 0:
+    // every block reads it before the finishing block counts) starts x from 0
+    const bool x0 = xfresh && ctl[C_IT] == 0;
     V xo[RPT], ro[RPT], pc[RPT], ac[RPT];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
         const int row = row0 + u * blockDim.y;
         if (i < g.nx && row < nrow) {
             const int c = i + g.nx * row;
-            xo[u] = x[c];
+            xo[u] = x0 ? V(0) : x[c];
             ro[u] = r[c];
             pc[u] = p[c];
             ac[u] = Ap[c];
@@ -1216,7 +1224,7 @@ __global__ void k_cg_update(GridD g, V *__restrict__ x, V *__restrict__ r, const
         if (i >= g.nx || row >= nrow) continue;
         const int c = i + g.nx * row;
         const int k = row / g.ny, j = row - k * g.ny;
-        x[c] = xo[u] + al * pc[u];
+        x[c] = x0 ? al * pc[u] : xo[u] + al * pc[u];
         const V rc = ro[u] - al * ac[u];
         r[c] = rc;
         z[c] = ((i + j + k) & 1) == 0 ? rc * id[u] : V(0);
@@ -1260,12 +1268,86 @@ __global__ void k_cg_pupdate(int n, const double *__restrict__ scal, const V *__
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) p[c] = z[c] + be * p[c];
 }
 
-// outer defect correction: q += e
-template <typename V>
-__global__ void k_cg_correct(int n, const V *__restrict__ e, double *__restrict__ q) {
-    griddep_wait();
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) q[c] += (double)e[c];
+// Error-free products (FMA) for the compensated operator below.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
 }
+
+// (M e)_c of an FP32 vector with FP32 coefficients as an unevaluated pair of
+// floats s + cc: each face difference (TwoSum) and product (TwoProduct) is
+// formed without rounding error and the terms are summed with TwoSum, so the
+// pair matches the exact row value to about 2^-46 of the sum of the term
+// magnitudes -- FP64-grade, with FP32 instructions only. Same faces as
+// poisson_row.
+template <int DIM>
+__device__ __forceinline__ void poisson_row_comp(const GridD &g, uint32_t inf, int c, int i, int j, int k,
+                                                 C3<float> cf, const float *__restrict__ e, float &s, float &cc) {
+    const float ec = e[c];
+    s = 0.f;
+    cc = 0.f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int off = noff(g, a);
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            const int t = ftype(inf, a, sd);
+            if (t != FT_INTERIOR && t != FT_OUTLET) continue;
+            const float w = cf.a[a][sd ? fhi(g, a, i, j, k) : flo(g, a, i, j, k)];
+            float p, pe, lo = 0.f;
+            if (t == FT_INTERIOR) {
+                float dh;
+                two_sum(ec, -e[sd ? c + off : c - off], dh, lo);
+                two_prod(w, dh, p, pe);
+                pe += w * lo;
+            } else {
+                two_prod(w, ec, p, pe);
+            }
+            float sn, se;
+            two_sum(s, p, sn, se);
+            s = sn;
+            cc += se + pe;
+        }
+    }
+}
+
+// End of an outer defect-correction trip (mixed path): q += e in FP64, and the
+// FP64 residual updated recursively, r64 -= M e, with M e from the
+// compensated apply above (so r64 stays b - M q to FP64 accuracy, without
+// re-evaluating the operator on q in FP64); then r = (float) r64, z = the
+// first colour-0 half sweep of the next V-cycle, ||r||^2, and the loop
+// decision of residual_control(mode 2).
+template <int DIM>
+__global__ void k_cg_refine(GridD g, const uint32_t *__restrict__ info, C3<float> cf, const float *__restrict__ e,
+                            double *__restrict__ q, double *__restrict__ r64, float *__restrict__ r,
+                            const float *__restrict__ idiag0, float *__restrict__ z, double *__restrict__ part,
+                            int stride, unsigned *__restrict__ ticket, int nb, double *__restrict__ scal,
+                            int *__restrict__ ctl, double rtol, cudaGraphConditionalHandle h) {
+    griddep_wait();
+    double rr = 0.0, dummy = 0.0;
+    ROW_LOOP(g) {
+        ROW_CELL(g);
+        if (i >= g.nx) continue;
+        const uint32_t inf = info[c];
+        float rv = 0.f;
+        if (inf & INFO_FLUID) {
+            float s, cc;
+            poisson_row_comp<DIM>(g, inf, c, i, j, k, cf, e, s, cc);
+            q[c] += (double)e[c];
+            const double rn = r64[c] - ((double)s + (double)cc);
+            r64[c] = rn;
+            rv = (float)rn;
+            rr = fma(rn, rn, rr);
+        }
+        r[c] = rv;
+        z[c] = ((i + j + k) & 1) == 0 ? rv * idiag0[c] : 0.f;
+    }
+    if (reduce_last(rr, dummy, 1, false, part, stride, ticket, nb) && block_leader()) {
+        scal[S_RR] = rr;
+        residual_control(scal, ctl, rtol, 2, h);
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // geometric multigrid (preconditioner): piecewise-constant transfers, coarse

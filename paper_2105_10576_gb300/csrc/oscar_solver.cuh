@@ -450,17 +450,17 @@ template <typename T> struct Impl {
     // decision of residual_control(mode)
     template <int DIM>
     static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h,
-                           V *zero1, V *zero2) {
+                           V *zero1, V *zero2, double *r64 = nullptr) {
         GridD g = to_dev(I.g);
         L3 L = launch_rows(I.g, kRedBlocks);
-        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, w64(I), q, b, (V *)I.cg_r,
+        launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, w64(I), q, b, (V *)I.cg_r, r64,
                 (const V *)I.lev[0].idiag, (V *)I.cg_z, zero1, zero2, I.partials, I.red_stride, I.ticket, L.nblocks,
                 I.scal, I.ctl, I.P.cg_rtol, mode, h), ++I.nlaunch;
     }
 
     // one PCG iteration on M x = r with Krylov vectors z, p, Ap (type V)
     template <int DIM>
-    static int pcg_body(Instance &I, V *x, int target_slot, cudaGraphConditionalHandle h) {
+    static int pcg_body(Instance &I, V *x, int target_slot, cudaGraphConditionalHandle h, int xfresh) {
         GridD g = to_dev(I.g);
         L3 L = launch_rows(I.g, kRedBlocks);
         int n = I.g.ncell;
@@ -482,7 +482,7 @@ template <typename T> struct Impl {
         prof_end(I, ps);
         L3 LU = launch_rpt(I.g, kUpdateRows);
         launchk(k_cg_update<V, kUpdateRows>, LU.grid, LU.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag,
-                z, I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, h), ++I.nlaunch;
+                z, I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, xfresh, h), ++I.nlaunch;
         if (I.capturing) {
             I.n_cg_body = I.nlaunch - n0;
             I.cg_bodies_captured += 1;
@@ -501,19 +501,27 @@ template <typename T> struct Impl {
             cudaGraphConditionalHandle h;
             OSCAR_TRY(cond_handle(I, &h));
             residual64<DIM>(I, q, b, 0, h, (V *)I.cg_p, nullptr);
-            return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h); });
+            return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h, 0); });
         } else {
         cudaGraphConditionalHandle ho;
         OSCAR_TRY(cond_handle(I, &ho));
-        residual64<DIM>(I, q, b, 1, ho, (V *)I.cg_e, (V *)I.cg_p);
+        // the inner solve starts e and p from 0 itself (xfresh, beta = 0), so
+        // neither is cleared; the FP64 residual is evaluated once, then updated
+        // by k_cg_refine at the end of every trip
+        residual64<DIM>(I, q, b, 1, ho, nullptr, nullptr, I.cg_r64);
         return loop_while(I, ho, [&]() -> int {
             long long n0 = I.nlaunch, cg0 = I.cg_bodies_captured;
             cudaGraphConditionalHandle hi;
             OSCAR_TRY(cond_handle(I, &hi));
             launchk(k_inner_start, 1, 1, 0, I.stream, I.scal, I.ctl, hi), ++I.nlaunch;
-            OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi); }));
-            launchk(k_cg_correct<V>, kRedBlocks, BS, 0, I.stream, I.g.ncell, (const V *)I.cg_e, q), ++I.nlaunch;
-            residual64<DIM>(I, q, b, 2, ho, (V *)I.cg_e, (V *)I.cg_p);
+            OSCAR_TRY(loop_while(I, hi, [&]() -> int { return pcg_body<DIM>(I, (V *)I.cg_e, S_ITARGET, hi, 1); }));
+            if constexpr (sizeof(V) == sizeof(float)) {
+                GridD g = to_dev(I.g);
+                L3 L = launch_rows(I.g, kRedBlocks);
+                launchk(k_cg_refine<DIM>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), (const float *)I.cg_e,
+                        q, I.cg_r64, (float *)I.cg_r, (const float *)I.lev[0].idiag, (float *)I.cg_z, I.partials,
+                        I.red_stride, I.ticket, L.nblocks, I.scal, I.ctl, I.P.cg_rtol, ho), ++I.nlaunch;
+            }
             if (I.capturing) I.n_outer_body = (I.nlaunch - n0) - (I.cg_bodies_captured - cg0) * I.n_cg_body;
             OSCAR_LAUNCH_CHECK();
             return 0;
