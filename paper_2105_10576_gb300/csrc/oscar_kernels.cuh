@@ -216,10 +216,10 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max) {
 }
 __device__ __forceinline__ double block_sum(double v) { return block_reduce(v, false); }
 __device__ __forceinline__ double block_max(double v) { return block_reduce(v, true); }
-// Compensated block sum of FP32 values: the (sum, rounding error) pair is
+// Compensated block sums of FP32 values: the (sum, rounding error) pair is
 // carried through the shuffle tree with error-free TwoSum steps (Knuth), so
 // the block total matches the FP64 sum of the thread values to about 2^-44
-// relative, with FP32 instructions only; returned in FP64 (valid in thread 0).
+// relative, with FP32 instructions only.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
     const float bb = s - a;
@@ -234,25 +234,21 @@ __device__ __forceinline__ void warp_sum_pair(float &s, float &e) {
         e += eo + err;
     }
 }
-__device__ __forceinline__ double block_sum_f(float v) {
+// block total of compensated pairs (s, e); the result is valid in thread 0
+__device__ __forceinline__ void block_pair_f(float &s, float &e) {
     __shared__ float shs[32], she[32];
     const int t = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
     const int w = t >> 5, l = t & 31, nw = nt >> 5;
-    float s = v, e = 0.f;
     warp_sum_pair(s, e);
     __syncthreads();
     if (l == 0) { shs[w] = s; she[w] = e; }
     __syncthreads();
-    double r = 0.0;
     if (w == 0) {
         s = l < nw ? shs[l] : 0.f;
         e = l < nw ? she[l] : 0.f;
         warp_sum_pair(s, e);
-        if (l == 0) r = (double)s + (double)e;
     }
-    return r;
 }
-
 // CG scalars: the finishing block stores alpha / beta in FP64 and an FP32
 // copy in the slot's f-twin, so FP32 kernels read them without FP64 work
 __device__ __forceinline__ void put_scalar(double *scal, int slot, int fslot, double v) {
@@ -315,11 +311,15 @@ __device__ __forceinline__ bool reduce_last(double &v0, double &v1, int nv, bool
 // block). An FP64 value goes through reduce_last.
 __device__ __forceinline__ bool reduce_last_sum(float v, double &out, double *__restrict__ part,
                                                 unsigned *__restrict__ ticket, int nb) {
-    const double bs = block_sum_f(v);
+    // block partials stay compensated pairs (stored as float2 in the FP64
+    // partial slots) and the finishing block sums them the same way, so the
+    // whole reduction runs in FP32 instructions up to the final FP64 sum
+    float s = v, e = 0.f;
+    block_pair_f(s, e);
     __shared__ int last_f;
     __shared__ double tot_f;
     if (block_leader()) {
-        part[BLOCK_ID()] = bs;
+        reinterpret_cast<float2 *>(part)[BLOCK_ID()] = make_float2(s, e);
         __threadfence();
         unsigned t = atomicAdd(ticket, 1u);
         last_f = (t == (unsigned)(nb - 1)) ? 1 : 0;
@@ -328,11 +328,17 @@ __device__ __forceinline__ bool reduce_last_sum(float v, double &out, double *__
     if (!last_f) return false;
     __threadfence();
     const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
-    double s0 = 0.0;
-    for (int q = tid; q < nb; q += nt) s0 += __ldcg(part + q);
-    s0 = block_sum(s0);
+    float as = 0.f, ae = 0.f;
+    for (int q = tid; q < nb; q += nt) {
+        const float2 pv = __ldcg(reinterpret_cast<const float2 *>(part) + q);
+        float sn, se;
+        two_sum(as, pv.x, sn, se);
+        as = sn;
+        ae += se + pv.y;
+    }
+    block_pair_f(as, ae);
     if (block_leader()) {
-        tot_f = s0;
+        tot_f = (double)as + (double)ae;
         *ticket = 0u;
     }
     __syncthreads();
@@ -1387,9 +1393,16 @@ __device__ __forceinline__ M mg_row_off(const GridD &g, const M *w, const M *x, 
 // one colour of a red-black Gauss-Seidel sweep; thread ti handles the cell
 // i = 2 ti + ((j + k + colour) & 1) of its row, so no thread idles. idiag is
 // 1 / diagonal on fluid cells and 0 elsewhere, so solid cells keep x = 0.
-template <int DIM, typename M>
+// PRO: the first post-smoothing half sweep with the prolongation folded in:
+// every neighbour value is read as x + xc(parent), which is what the
+// piecewise-constant prolongation would have stored (faces to solid cells
+// have zero coefficients, so their values do not matter). The other colour
+// is never read before the next half sweep overwrites it, so the prolonged
+// field itself is not stored.
+template <int DIM, typename M, bool PRO>
 __global__ void k_mg_rbgs(GridD g, MG3<M> cc, const M *__restrict__ idiag, M *__restrict__ x,
-                          const M *__restrict__ b, int colour) {
+                          const M *__restrict__ b, int colour, GridD gc, int s0, int s1, int s2,
+                          const M *__restrict__ xc) {
     const int ti = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
@@ -1403,7 +1416,28 @@ __global__ void k_mg_rbgs(GridD g, MG3<M> cc, const M *__restrict__ idiag, M *__
     }
     griddep_wait();
     if (!ok) return;
-    x[cell] = (b[cell] + mg_row_off<DIM, M>(g, w, x, cell, i, j, k)) * id;
+    M off;
+    if constexpr (PRO) {
+        const int ijk[3] = {i, j, k}, n[3] = {g.nx, g.ny, g.nz}, sh[3] = {s0, s1, s2};
+        const int pc[3] = {i >> s0, j >> s1, k >> s2};
+        off = M(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int o = noff(g, a);
+#pragma unroll
+            for (int sd = 0; sd < 2; ++sd) {
+                const bool in = sd ? ijk[a] < n[a] - 1 : ijk[a] > 0;
+                if (!in) continue;
+                int pp[3] = {pc[0], pc[1], pc[2]};
+                pp[a] = (ijk[a] + (sd ? 1 : -1)) >> sh[a];
+                const M v = x[sd ? cell + o : cell - o] + xc[pp[0] + gc.nx * (pp[1] + gc.ny * pp[2])];
+                off += w[2 * a + sd] * v;
+            }
+        }
+    } else {
+        off = mg_row_off<DIM, M>(g, w, x, cell, i, j, k);
+    }
+    x[cell] = (b[cell] + off) * id;
 }
 
 // The last half sweep of the finest level (colour 0) fused with r.z: the
@@ -1486,18 +1520,6 @@ __global__ void k_mg_resid_restrict(GridD gf, GridD gc, const uint8_t *__restric
     }
     bc[c] = acc;
     xc[c] = (first && ((i + j + k) & 1) == 0) ? acc * idq : M(0);
-}
-
-template <typename M>
-__global__ void k_mg_prolong(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ fluid,
-                             const M *__restrict__ xc, M *__restrict__ x) {
-    CELL_IJK(gf);
-    const uint8_t f = inside ? fluid[c] : 0;
-    griddep_wait();
-    if (!inside) return;
-    const M v = xc[(i / rx) + gc.nx * ((j / ry) + gc.ny * (k / rz))];
-    const M xo = x[c];
-    if (f) x[c] = xo + v;
 }
 
 static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ ff,

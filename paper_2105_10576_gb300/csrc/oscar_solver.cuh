@@ -364,9 +364,19 @@ template <typename T> struct Impl {
             launchk(k_mg_rbgs_dot<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour,
                     I.partials, I.ticket, I.scal), ++I.nlaunch;
         else
-            launchk(k_mg_rbgs<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour),
-                ++I.nlaunch;
+            launchk(k_mg_rbgs<DIM, M, false>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b,
+                    colour, g, 0, 0, 0, (const M *)nullptr), ++I.nlaunch;
         prof_end(I, ps);
+    }
+    // the first post-smoothing half sweep (colour 1) of level l with the
+    // prolongation from level l + 1 (x of level l + 1 in xc) folded in
+    template <int DIM>
+    static void prolong_smooth(Instance &I, int l, M *x, const M *b, const M *xc) {
+        Level &L = I.lev[l], &C = I.lev[l + 1];
+        GridD g = to_dev(L.g), gc = to_dev(C.g);
+        L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
+        launchk(k_mg_rbgs<DIM, M, true>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, 1, gc,
+                L.r[0] >> 1, L.r[1] >> 1, L.r[2] >> 1, xc), ++I.nlaunch;
     }
 
     template <int DIM, int RX, int RY, int RZ>
@@ -430,15 +440,11 @@ template <typename T> struct Impl {
             launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P), ++I.nlaunch;
         }
         for (int l = lk - 1; l >= 0; --l) {
-            Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
             int nu = l == 0 ? I.mg_nu : I.mg_nu_c;
-            GridD g = to_dev(L.g), gc = to_dev(C.g);
-            L3 LL = launch3(L.g);
-            launchk(k_mg_prolong<M>, LL.grid, LL.block, 0, I.stream, g, gc, L.r[0], L.r[1], L.r[2], L.fluid,
-                                                                (const M *)lx(I, l + 1, z), x), ++I.nlaunch;
             for (int s = 0; s < nu; ++s) {
-                smooth_level<DIM>(I, l, 1, x, b);
+                if (s == 0) prolong_smooth<DIM>(I, l, x, b, (const M *)lx(I, l + 1, z));
+                else smooth_level<DIM>(I, l, 1, x, b);
                 smooth_level<DIM>(I, l, 0, x, b, l == 0 && s == nu - 1);   // the last one also forms r.z
             }
         }
