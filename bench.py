@@ -291,6 +291,57 @@ def time_to_solution():
     return res
 
 
+def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
+    """The batched relaxation sweep (config 3): 64 bubble channels, grids drawn
+    from {128x16 .. 1024x128}, Ca log-uniform in [1e-6, 1e-3], bubble length
+    2-5 widths (seed 0). A step of an instance is one drag step of 50 dt_cr
+    followed by up to 50 relaxation sub-steps of dt_cr = 0.99 dt_Brackbill
+    (early exit at max|du_cr|/U < 1e-6), pressure solves to 1e-8. Mixed
+    precision, all instances stepped concurrently (batch.Batch), against the
+    same instances in FP64 stepped one at a time; one untimed warm-up step
+    each (graph construction). Wall-clock seconds through the C ABI."""
+    from paper_2105_10576_gb300 import batch as bt
+    from paper_2105_10576_gb300 import oscar as ox
+    cases = inputs.batched_sweep(n_inst, seed=0)
+    res = {"workload": f"{n_inst} 2D bubble channels (config 3 generator, seed 0), grids 128x16..1024x128, "
+                       f"Ca 1e-6..1e-3; step = drag + up to {n_sub} sub-steps at 0.99 dt_B",
+           "unit": UNIT, "steps": steps}
+    out = {}
+    for mode, prec in (("batched_mixed", inputs.PREC_MIXED), ("sequential_fp64", inputs.PREC_FP64)):
+        sims, dtv, dtc = [], [], []
+        for c in cases:
+            p = dict(c.params, precision=prec, cg_rtol=1e-8)
+            dt_cfl, dt_b, _, _ = ox.oscar_timesteps(p, c.meta["c_cfl"])
+            dtc.append(0.99 * dt_b)
+            dtv.append(n_sub * 0.99 * dt_b)
+            sims.append(ox.Oscar(p, c.solid, c.alpha0))
+        nf = [s.stats()["n_fluid"] for s in sims]
+        b = bt.Batch(sims)
+
+        def one_step():
+            if mode == "batched_mixed":
+                return b.step(dtv, dtc, [n_sub] * n_inst)
+            kfs = []
+            for s, dv, dc in zip(sims, dtv, dtc):
+                s.drag_step(dv, strict=False)
+                kfs.append(s.relax(dc, n_sub, strict=False)[1])
+            return kfs
+
+        one_step()
+        t0 = time.perf_counter()
+        cu = 0
+        for _ in range(steps):
+            kfs = one_step()
+            cu += sum(n * (1 + k) for n, k in zip(nf, kfs))
+        dt = time.perf_counter() - t0
+        out[mode] = {"value": cu / dt, "seconds": dt, "cell_updates": cu,
+                     "device_bytes": int(sum(s.stats()["device_bytes"] for s in sims))}
+        b.close()
+    res.update(out)
+    res["batched_mixed_over_sequential_fp64"] = out["batched_mixed"]["value"] / out["sequential_fp64"]["value"]
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +354,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the OSCAR vs standard time-to-solution runs")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison (64 instances)")
     args = ap.parse_args()
     c, desc = make_workload(args.workload)
 
@@ -441,6 +493,9 @@ def main():
     tts = None
     if rank == 0 and not args.no_tts:
         tts = time_to_solution()
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_sweep()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -455,7 +510,8 @@ def main():
                            "l2": "working set larger than L2 (no flush needed)",
                            "device_bytes": int(s_after["device_bytes"])},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
-                "gpu_launches": int(launches), "clocks": clk, "time_to_solution": tts}
+                "gpu_launches": int(launches), "clocks": clk, "time_to_solution": tts,
+                "batched": batched}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

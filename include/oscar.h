@@ -139,6 +139,26 @@ int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_
  * fields (u_vd, p_vd, phi_vd) hold u, p, phi and the relaxation fields stay 0. */
 int oscar_standard_step(oscar_handle h, double dt);
 
+/* Asynchronous forms of the three steps: each validates its arguments, launches
+ * the step on the handle's stream (one CUDA graph launch, plus the copies of its
+ * loop counters back to pinned host memory) and returns without waiting, so that
+ * the steps of many handles, each on its own stream, run at the same time on the
+ * GPU. A handle with a launched step accepts only oscar_wait and oscar_destroy
+ * (every other call returns OSCAR_E_INVALID_ARG) until oscar_wait has collected
+ * it. Arguments and errors as for the synchronous calls; launch failures are
+ * returned here, the step's own status by oscar_wait. These belong to the
+ * serving/batching layer, not to the paper's method. */
+int oscar_drag_step_async(oscar_handle h, double dt_vd);
+int oscar_relax_async(oscar_handle h, double dt_cr, int N);
+int oscar_standard_step_async(oscar_handle h, double dt);
+
+/* Wait (bounded, OSCAR_E_TIMEOUT after 600 s) for the step launched by an
+ * *_async call and return its status as the synchronous call would. k_f_out
+ * (may be NULL) receives k_f for a relaxation, 1 otherwise; test_out (may be
+ * NULL) the last test value of a relaxation, else the step's E. Returns
+ * OSCAR_E_INVALID_ARG when no step is pending. */
+int oscar_wait(oscar_handle h, int *k_f_out, double *test_out);
+
 /* Copy one field to host memory (double). n must equal the field's length
  * (ncell, or the face count of its direction). Waits for the stream. */
 int oscar_fields(oscar_handle h, int which, double *host_out, size_t n);

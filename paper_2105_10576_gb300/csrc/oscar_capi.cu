@@ -259,6 +259,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.cos_theta = cos(p->theta_deg * M_PI / 180.0);
     I.deltaN = 1e-8 / pow(I.g.V, 1.0 / p->dim);
     I.last_N = 1;
+    I.pending = -1;
     I.mg_nu = 2;
     I.mg_nu_c = 2;
     I.mg_coarse_sweeps = 4;
@@ -343,15 +344,47 @@ int oscar_destroy(oscar_handle h) {
     return 0;
 }
 
+int oscar_drag_step_async(oscar_handle h, double dt_vd) {
+    if (!h || !(dt_vd > 0)) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::launch_step(I, 0, dt_vd, 1) : Solver<float>::launch_step(I, 0, dt_vd, 1);
+}
+
+int oscar_relax_async(oscar_handle h, double dt_cr, int N) {
+    if (!h || !(dt_cr > 0) || N < 1) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;
+    if (I.P.conv_mode == OSCAR_CONV_DU_MAX && !(I.P.U_inlet > 0)) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::launch_step(I, 1, dt_cr, N) : Solver<float>::launch_step(I, 1, dt_cr, N);
+}
+
+int oscar_standard_step_async(oscar_handle h, double dt) {
+    if (!h || !(dt > 0)) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::launch_step(I, 2, dt, 1) : Solver<float>::launch_step(I, 2, dt, 1);
+}
+
+int oscar_wait(oscar_handle h, int *k_f_out, double *test_out) {
+    if (!h) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending < 0) return OSCAR_E_INVALID_ARG;
+    return I.prec == OSCAR_FP64 ? Solver<double>::finish_step(I, k_f_out, test_out)
+                                : Solver<float>::finish_step(I, k_f_out, test_out);
+}
+
 int oscar_drag_step(oscar_handle h, double dt_vd) {
     if (!h || !(dt_vd > 0)) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     return I.prec == OSCAR_FP64 ? Solver<double>::drag_step(I, dt_vd) : Solver<float>::drag_step(I, dt_vd);
 }
 
 int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_out) {
     if (!h || !(dt_cr > 0) || N < 1) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     if (I.P.conv_mode == OSCAR_CONV_DU_MAX && !(I.P.U_inlet > 0)) return OSCAR_E_INVALID_ARG;
     return I.prec == OSCAR_FP64 ? Solver<double>::relax(I, dt_cr, N, k_f_out, test_out)
                                 : Solver<float>::relax(I, dt_cr, N, k_f_out, test_out);
@@ -360,12 +393,14 @@ int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_
 int oscar_standard_step(oscar_handle h, double dt) {
     if (!h || !(dt > 0)) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     return I.prec == OSCAR_FP64 ? Solver<double>::standard_step(I, dt) : Solver<float>::standard_step(I, dt);
 }
 
 int oscar_fields_device(oscar_handle h, int which, double *dev_out, size_t n) {
     if (!h || !dev_out) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     size_t len = field_len(I, which);
     if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
     return I.prec == OSCAR_FP64 ? Solver<double>::field_to_device(I, which, dev_out, n)
@@ -375,6 +410,7 @@ int oscar_fields_device(oscar_handle h, int which, double *dev_out, size_t n) {
 int oscar_fields(oscar_handle h, int which, double *host_out, size_t n) {
     if (!h || !host_out) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     size_t len = field_len(I, which);
     if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
     int rc = I.prec == OSCAR_FP64 ? Solver<double>::field_to_device(I, which, I.stage_dev, len)
@@ -392,6 +428,7 @@ int oscar_fields(oscar_handle h, int which, double *host_out, size_t n) {
 int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n) {
     if (!h || !host_in) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     size_t len = field_len(I, which);
     if (len == 0 || n != len) return OSCAR_E_INVALID_ARG;
     int rc = sync_bounded(I.stream, kSyncTimeoutSec);
@@ -409,6 +446,7 @@ int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n) 
 int oscar_stats(oscar_handle h, oscar_stats_t *out) {
     if (!h || !out) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     double vol = 0.0;
     int rc = I.prec == OSCAR_FP64 ? Solver<double>::phase_volume(I, &vol) : Solver<float>::phase_volume(I, &vol);
     if (rc) return rc;
@@ -436,6 +474,7 @@ extern "C" {
 int oscar_profile(oscar_handle h, int enable) {
     if (!h) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     if (!I.prof) {
         I.prof = new (std::nothrow) Profiler();
         if (!I.prof) return OSCAR_E_OOM;
@@ -455,6 +494,7 @@ int oscar_profile(oscar_handle h, int enable) {
 int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms) {
     if (!h || !avg_ms || reps < 1 || kid < 0 || kid >= OSCAR_KID_COUNT) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
     return I.prec == OSCAR_FP64 ? Solver<double>::profile_kernel(I, kid, reps, avg_ms)
                                 : Solver<float>::profile_kernel(I, kid, reps, avg_ms);
 }

@@ -102,6 +102,9 @@ struct Instance {
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     size_t cta_smem;       // shared memory of the coarse kernel
     int lA;                // first level of the cluster kernel (mixed path), -1 when it is not used
+    int pending;           // kind (0 drag, 1 relax, 2 standard) of a launched step not yet waited for, or -1
+    double pending_dt;
+    int pending_N;
     size_t cl_smem;        // shared memory per CTA of the cluster kernel
     unsigned *ticket;      // block counter of the single-pass reductions (0 between kernels)
     double *scal;          // S_COUNT device scalars
@@ -144,6 +147,8 @@ template <typename T> struct Solver {
     static int drag_step(Instance &I, double dt);
     static int relax(Instance &I, double dt, int N, int *kf, double *test);
     static int standard_step(Instance &I, double dt);
+    static int launch_step(Instance &I, int kind, double dt, int N);   // no wait
+    static int finish_step(Instance &I, int *kf, double *test);       // waits for the launched step
     static int field_to_device(Instance &I, int which, double *dst, size_t n);
     static int field_from_device(Instance &I, int which, const double *src, size_t n);
     static int phase_volume(Instance &I, double *out);

@@ -737,7 +737,9 @@ template <typename T> struct Impl {
     }
 
     // Launch step `kind` (graph, or eager loops) and read its control words back.
-    static int run(Instance &I, int kind, double dt, int N) {
+    // launch one step (graph, or the eager sequence) and the copies of its
+    // device scalars back to the host, without waiting
+    static int run_launch(Instance &I, int kind, double dt, int N) {
         if (!I.eager) OSCAR_TRY(build(I, kind, dt));
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
         for (int q = 0; q < C_COUNT; ++q) I.ctl_host[q] = 0;
@@ -755,6 +757,20 @@ template <typename T> struct Impl {
             cudaMemcpyAsync(I.ctl_host, I.ctl, C_COUNT * sizeof(int), cudaMemcpyDeviceToHost, I.stream) !=
                 cudaSuccess)
             return OSCAR_E_CUDA;
+        I.pending = kind;
+        I.pending_dt = dt;
+        I.pending_N = N;
+        return 0;
+    }
+    static int run(Instance &I, int kind, double dt, int N) {
+        OSCAR_TRY(run_launch(I, kind, dt, N));
+        return run_finish(I);
+    }
+    // wait for the launched step and account for it
+    static int run_finish(Instance &I) {
+        const int kind = I.pending;
+        const double dt = I.pending_dt;
+        I.pending = -1;
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));
         const GraphSlot &G = I.gslot[kind];
         int its = I.ctl_host[C_ITSUM];
@@ -863,6 +879,30 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
 }
 
 template <typename T> int Solver<T>::drag_step(Instance &I, double dt) { return Impl<T>::run(I, 0, dt, 1); }
+
+template <typename T> int Solver<T>::launch_step(Instance &I, int kind, double dt, int N) {
+    int rc = Impl<T>::run_launch(I, kind, dt, N);
+    if (rc) I.pending = -1;
+    return rc;
+}
+
+template <typename T> int Solver<T>::finish_step(Instance &I, int *kf_out, double *test_out) {
+    const int kind = I.pending, N = I.pending_N;
+    int rc = Impl<T>::run_finish(I);
+    if (rc == OSCAR_E_CUDA || rc == OSCAR_E_TIMEOUT) return rc;
+    if (kind == 1) {
+        I.last_kf = I.ctl_host[C_K];
+        I.last_N = N;
+        I.last_E = I.scal_host[S_E];
+        I.last_dU = I.scal_host[S_DU];
+    } else if (kind == 2) {
+        I.last_E = I.scal_host[S_E];
+        I.last_N = 1;
+    }
+    if (kf_out) *kf_out = kind == 1 ? I.ctl_host[C_K] : 1;
+    if (test_out) *test_out = kind == 1 ? I.scal_host[S_TEST] : I.scal_host[S_E];
+    return rc;
+}
 
 template <typename T> int Solver<T>::relax(Instance &I, double dt, int N, int *kf_out, double *test_out) {
     int rc = Impl<T>::run(I, 1, dt, N);

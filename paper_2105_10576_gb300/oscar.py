@@ -53,6 +53,7 @@ class oscar_stats_t(C.Structure):
 
 
 EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", "oscar_standard_step",
+           "oscar_drag_step_async", "oscar_relax_async", "oscar_standard_step_async", "oscar_wait",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
            "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel",
            "oscar_phase_volume_noalloc"]
@@ -76,6 +77,10 @@ def load(path: str = LIB_PATH):
     lib.oscar_drag_step.argtypes = [H, C.c_double]
     lib.oscar_relax.argtypes = [H, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
     lib.oscar_standard_step.argtypes = [H, C.c_double]
+    lib.oscar_drag_step_async.argtypes = [H, C.c_double]
+    lib.oscar_relax_async.argtypes = [H, C.c_double, C.c_int]
+    lib.oscar_standard_step_async.argtypes = [H, C.c_double]
+    lib.oscar_wait.argtypes = [H, C.POINTER(C.c_int), dp]
     lib.oscar_fields.argtypes = [H, C.c_int, dp, C.c_size_t]
     lib.oscar_fields_device.argtypes = [H, C.c_int, C.c_void_p, C.c_size_t]
     lib.oscar_set_field.argtypes = [H, C.c_int, dp, C.c_size_t]
@@ -161,6 +166,22 @@ class Oscar:
         kf = C.c_int(0)
         test = C.c_double(0.0)
         rc = _check(self.lib.oscar_relax(self.h, dt_cr, N, C.byref(kf), C.byref(test)), "oscar_relax", not strict)
+        return rc, kf.value, test.value
+
+    # asynchronous steps: launch now, collect with wait() (one pending step per handle)
+    def drag_step_async(self, dt: float) -> int:
+        return _check(self.lib.oscar_drag_step_async(self.h, dt), "oscar_drag_step_async")
+
+    def relax_async(self, dt_cr: float, N: int) -> int:
+        return _check(self.lib.oscar_relax_async(self.h, dt_cr, N), "oscar_relax_async")
+
+    def standard_step_async(self, dt: float) -> int:
+        return _check(self.lib.oscar_standard_step_async(self.h, dt), "oscar_standard_step_async")
+
+    def wait(self, strict: bool = True):
+        kf = C.c_int(0)
+        test = C.c_double(0.0)
+        rc = _check(self.lib.oscar_wait(self.h, C.byref(kf), C.byref(test)), "oscar_wait", not strict)
         return rc, kf.value, test.value
 
     def standard_step(self, dt: float, strict: bool = True) -> int:
