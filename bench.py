@@ -342,6 +342,59 @@ def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
     return res
 
 
+def serving(seconds: float = 10.0, rate: float = 20.0, seed: int = 0, n_sub: int = 5, steps: int = 1,
+            budget_gb: float = 150.0):
+    """The serving stream (config 4), over a shortened arrival window: Poisson
+    arrivals (rate 20/s, seeded), half 2D disc micromodels (512x256, 1024x512 or
+    2048x1024; Ca log-uniform in [1e-6, 1e-4]; one geometry per size, drawn
+    before the clock starts), half 3D constricted channels (64^3, 128x64x64,
+    256x64x64 or 256x128x128; throat 20-50 %; Ca log-uniform in [1e-6, 1e-4]);
+    mixed precision; each request is `steps` OSCAR steps of one drag step of
+    n_sub dt_cr and up to n_sub relaxation sub-steps of dt_cr = 0.99 dt_B.
+    Admission by memory footprint under a 150 GB budget (serve.Server)."""
+    from paper_2105_10576_gb300 import oscar as ox
+    from paper_2105_10576_gb300 import serve as sv
+    rng = np.random.default_rng(seed)
+    micro_sizes = [(512, 256), (1024, 512), (2048, 1024)]
+    chan_sizes = [(64, 64, 64), (128, 64, 64), (256, 64, 64), (256, 128, 128)]
+    micro_pool = {sz: inputs.micromodel_2d(nx=sz[0], ny=sz[1], seed=seed + 1) for sz in micro_sizes}
+    reqs = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > seconds:
+            break
+        Ca = 10.0 ** rng.uniform(-6, -4)
+        if rng.random() < 0.5:
+            base = micro_pool[micro_sizes[int(rng.integers(len(micro_sizes)))]]
+            U = Ca * base.params["sigma"] / 1e-3
+            p = dict(base.params, U_inlet=U)
+            solid, alpha0 = base.solid, base.alpha0
+        else:
+            nx, ny, nz = chan_sizes[int(rng.integers(len(chan_sizes)))]
+            c = inputs.constricted_channel_3d(nx=nx, ny=ny, nz=nz, Ca=Ca, throat=float(rng.uniform(0.2, 0.5)))
+            p, solid, alpha0 = dict(c.params), c.solid, c.alpha0
+        p.update(precision=inputs.PREC_MIXED, cg_rtol=1e-8)
+        dt_b = ox.oscar_timesteps(p, 0.1)[1]
+        reqs.append(sv.Request(len(reqs), t, p, solid, alpha0, n_sub * 0.99 * dt_b, 0.99 * dt_b, n_sub, steps))
+    srv = sv.Server(int(budget_gb * 1e9))
+    t0 = time.perf_counter()
+    recs = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    done = [r for r in recs if r.status != -1]
+    tts = np.array([r.time_to_solution for r in done])
+    cu = sum(r.cell_updates for r in done)
+    return {"workload": f"Poisson arrivals {rate:g}/s over {seconds:g} s (seed {seed}), 50 % 2D micromodels "
+                        "512x256..2048x1024, 50 % 3D constrictions 64^3..256x128x128, Ca 1e-6..1e-4, "
+                        f"{steps} step(s) of drag + up to {n_sub} sub-steps each, mixed precision, 150 GB budget",
+            "requests": len(reqs), "completed": len(done),
+            "p50_time_to_solution_s": float(np.percentile(tts, 50)) if len(tts) else None,
+            "p99_time_to_solution_s": float(np.percentile(tts, 99)) if len(tts) else None,
+            "aggregate_cell_updates_per_s": cu / wall, "wall_s": wall,
+            "max_concurrent": srv.max_concurrent, "max_resident_bytes": srv.max_used,
+            "not_converged_requests": sum(1 for r in done if r.status == -3)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,6 +408,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the OSCAR vs standard time-to-solution runs")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison (64 instances)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run (Poisson arrivals)")
+    ap.add_argument("--serving-seconds", type=float, default=10.0, help="arrival window of the serving run")
     args = ap.parse_args()
     c, desc = make_workload(args.workload)
 
@@ -496,6 +551,9 @@ def main():
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_sweep()
+    serving_res = None
+    if rank == 0 and not args.no_serving:
+        serving_res = serving(seconds=args.serving_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -511,7 +569,7 @@ def main():
                            "device_bytes": int(s_after["device_bytes"])},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "time_to_solution": tts,
-                "batched": batched}
+                "batched": batched, "serving": serving_res}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

@@ -139,6 +139,12 @@ int oscar_relax(oscar_handle h, double dt_cr, int N, int *k_f_out, double *test_
  * fields (u_vd, p_vd, phi_vd) hold u, p, phi and the relaxation fields stay 0. */
 int oscar_standard_step(oscar_handle h, double dt);
 
+/* Device memory (bytes) that oscar_create would allocate for these parameters,
+ * from the same layout computation and without allocating anything (for
+ * admission control by memory footprint). Errors as oscar_create's parameter
+ * validation. Not part of the paper's method. */
+int oscar_footprint(const oscar_params *p, size_t *bytes_out);
+
 /* Asynchronous forms of the three steps: each validates its arguments, launches
  * the step on the handle's stream (one CUDA graph launch, plus the copies of its
  * loop counters back to pinned host memory) and returns without waiting, so that
@@ -151,6 +157,11 @@ int oscar_standard_step(oscar_handle h, double dt);
 int oscar_drag_step_async(oscar_handle h, double dt_vd);
 int oscar_relax_async(oscar_handle h, double dt_cr, int N);
 int oscar_standard_step_async(oscar_handle h, double dt);
+
+/* Non-blocking check of the step launched by an *_async call: 1 when it has
+ * finished (oscar_wait then returns at once), 0 while it runs, OSCAR_E_INVALID_ARG
+ * when no step is pending, OSCAR_E_CUDA on a stream error. */
+int oscar_query(oscar_handle h);
 
 /* Wait (bounded, OSCAR_E_TIMEOUT after 600 s) for the step launched by an
  * *_async call and return its status as the synchronous call would. k_f_out

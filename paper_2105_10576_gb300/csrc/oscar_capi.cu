@@ -229,6 +229,37 @@ const char *oscar_strerror(int code) {
     }
 }
 
+// grid, multigrid hierarchy and arena layout of an instance (no allocation)
+static void plan(Instance &I, const oscar_params *p) {
+    I.P = *p;
+    I.prec = p->precision;
+    I.g = make_grid(p->dim, p->nx, p->ny, p->nz, p->hx, p->hy, p->hz);
+    build_hierarchy(I);
+    int bx = I.g.nx >= 256 ? 256 : (I.g.nx > 64 ? 128 : (I.g.nx > 32 ? 64 : 32));
+    int by = 256 / bx;
+    long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
+    I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
+    size_t stage = I.g.ncell;
+    for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];
+    I.stage_len = stage;
+    Carver dry{nullptr, 0, true};
+    carve(I, dry);
+    I.arena_bytes = dry.off + 256;
+}
+
+int oscar_footprint(const oscar_params *p, size_t *bytes_out) {
+    if (!bytes_out) return OSCAR_E_INVALID_ARG;
+    int rc = validate(p);
+    if (rc) return rc;
+    Instance *I = new (std::nothrow) Instance();
+    if (!I) return OSCAR_E_OOM;
+    memset(I, 0, sizeof(Instance));
+    plan(*I, p);
+    *bytes_out = I->arena_bytes;
+    delete I;
+    return 0;
+}
+
 int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alpha0, void *stream,
                  oscar_handle *out) {
     if (!out) return OSCAR_E_INVALID_ARG;
@@ -364,6 +395,17 @@ int oscar_standard_step_async(oscar_handle h, double dt) {
     Instance &I = h->I;
     if (I.pending >= 0) return OSCAR_E_INVALID_ARG;
     return I.prec == OSCAR_FP64 ? Solver<double>::launch_step(I, 2, dt, 1) : Solver<float>::launch_step(I, 2, dt, 1);
+}
+
+int oscar_query(oscar_handle h) {
+    if (!h) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending < 0) return OSCAR_E_INVALID_ARG;
+    cudaError_t e = cudaStreamQuery(I.stream);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    cudaGetLastError();
+    return OSCAR_E_CUDA;
 }
 
 int oscar_wait(oscar_handle h, int *k_f_out, double *test_out) {

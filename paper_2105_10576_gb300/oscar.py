@@ -54,6 +54,7 @@ class oscar_stats_t(C.Structure):
 
 EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", "oscar_standard_step",
            "oscar_drag_step_async", "oscar_relax_async", "oscar_standard_step_async", "oscar_wait",
+           "oscar_footprint", "oscar_query",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
            "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel",
            "oscar_phase_volume_noalloc"]
@@ -81,6 +82,8 @@ def load(path: str = LIB_PATH):
     lib.oscar_relax_async.argtypes = [H, C.c_double, C.c_int]
     lib.oscar_standard_step_async.argtypes = [H, C.c_double]
     lib.oscar_wait.argtypes = [H, C.POINTER(C.c_int), dp]
+    lib.oscar_footprint.argtypes = [C.POINTER(oscar_params), C.POINTER(C.c_size_t)]
+    lib.oscar_query.argtypes = [H]
     lib.oscar_fields.argtypes = [H, C.c_int, dp, C.c_size_t]
     lib.oscar_fields_device.argtypes = [H, C.c_int, C.c_void_p, C.c_size_t]
     lib.oscar_set_field.argtypes = [H, C.c_int, dp, C.c_size_t]
@@ -109,6 +112,14 @@ def _check(rc: int, where: str, allow_not_converged: bool = False):
     if rc == 0 or (allow_not_converged and rc == -3):
         return rc
     raise OscarError(rc, where)
+
+
+def oscar_footprint(params: dict) -> int:
+    """Device bytes an instance with these parameters would hold (no allocation)."""
+    lib = load()
+    out = C.c_size_t(0)
+    _check(lib.oscar_footprint(C.byref(make_params(params)), C.byref(out)), "oscar_footprint")
+    return int(out.value)
 
 
 def oscar_timesteps(params: dict, c_cfl: float):
@@ -177,6 +188,13 @@ class Oscar:
 
     def standard_step_async(self, dt: float) -> int:
         return _check(self.lib.oscar_standard_step_async(self.h, dt), "oscar_standard_step_async")
+
+    def query(self) -> bool:
+        """True when the launched step has finished (wait() then returns at once)."""
+        rc = self.lib.oscar_query(self.h)
+        if rc < 0:
+            raise OscarError(rc, "oscar_query")
+        return rc == 1
 
     def wait(self, strict: bool = True):
         kf = C.c_int(0)

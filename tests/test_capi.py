@@ -65,3 +65,18 @@ def test_create_rejects_bad_arguments(lib):
     assert rc == -1 and not h.value
     assert lib.oscar_drag_step(None, 1.0) == -1
     assert lib.oscar_relax(None, 1.0, 3, None, None) == -1
+
+
+def test_footprint_is_host_only_and_scales(lib):
+    """oscar_footprint computes the arena size without a GPU: it grows with the
+    grid, and the FP64 path needs more than the mixed path."""
+    c = inputs.constricted_channel_3d(nx=64, ny=16, nz=16)
+    mixed = oscar.oscar_footprint(dict(c.params, precision=inputs.PREC_MIXED))
+    fp64 = oscar.oscar_footprint(dict(c.params, precision=inputs.PREC_FP64))
+    big = oscar.oscar_footprint(dict(inputs.constricted_channel_3d(nx=128, ny=32, nz=32).params,
+                                     precision=inputs.PREC_MIXED))
+    n = 64 * 16 * 16
+    assert 50 * n < mixed < fp64 < 2000 * n
+    assert 7 * mixed < big < 9 * mixed
+    with pytest.raises(oscar.OscarError):
+        oscar.oscar_footprint(dict(c.params, nx=0))

@@ -251,6 +251,34 @@ def test_batched_instances_match_alone():
         g.close()
 
 
+def test_serving_results_match_alone():
+    """Requests admitted while others run (staggered arrivals, a memory budget
+    that holds only some of them at once) finish with exactly the fields they
+    give when run alone, and the admission never exceeds the budget."""
+    from paper_2105_10576_gb300 import serve
+    cases = inputs.batched_sweep(5, seed=4, grids=((128, 16), (256, 32)))
+    reqs = []
+    for q, c in enumerate(cases):
+        p, dtv, dtc = _batch_setup(c, 4)
+        reqs.append(serve.Request(q, 0.02 * q, p, c.solid, c.alpha0, dtv, dtc, 4, 2))
+    fps = [ox.oscar_footprint(r.params) for r in reqs]
+    g = ox.Oscar(reqs[0].params, reqs[0].solid, reqs[0].alpha0)
+    assert fps[0] == g.stats()["device_bytes"]     # the footprint is what create allocates
+    g.close()
+    budget = max(fps) + min(fps)                      # not all of them fit at once
+    assert sum(fps) > budget
+    srv = serve.Server(budget)
+    recs = srv.run(reqs, keep_alpha=True)
+    assert srv.max_concurrent >= 2 and srv.max_used <= budget
+    assert [r.rid for r in recs] == list(range(len(reqs)))
+    for r, rec in zip(reqs, recs):
+        alone = serve.run_alone(r)
+        assert rec.status in (0, -3) and rec.k_f == alone.k_f
+        assert rec.cell_updates == alone.cell_updates
+        assert np.array_equal(rec.alpha, alone.alpha)
+        assert rec.done >= rec.admitted >= rec.arrival
+
+
 def test_edge_cases():
     # all-solid grid is rejected; a single fluid column works
     c = inputs.random_small_case(6, 5, 4)
