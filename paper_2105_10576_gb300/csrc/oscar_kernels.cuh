@@ -362,7 +362,7 @@ __device__ __forceinline__ void set_cond(int *ctl, cudaGraphConditionalHandle h,
 
 // after r = b - M q: mode 0 = start of a plain PCG solve; 1 / 2 = first /
 // later check of the defect-correction loop (mixed path)
-constexpr int kMaxOuter = 10;          // defect-correction trips (mixed path)
+constexpr int kMaxOuter = 40;          // defect-correction trips (mixed path)
 constexpr double kInnerRtol = 1e-4;    // FP32 inner solve: residual reduction per trip
 __device__ __forceinline__ void residual_control(double *scal, int *ctl, double rtol, int mode,
                                                  cudaGraphConditionalHandle h) {

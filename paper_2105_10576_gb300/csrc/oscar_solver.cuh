@@ -825,10 +825,13 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
     while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= cap && Impl<T>::cta_levels(I, P, I.lc0 - 1) <= budget) --I.lc0;
     I.cta_smem = Impl<T>::cta_levels(I, P, I.lc0);
     if (I.cta_smem > budget) return OSCAR_E_INVALID_ARG;
+    // the attribute belongs to the kernel, not to this instance: it is set to
+    // the budget (never lowered), so that instances of other sizes, created
+    // while this one runs, cannot shrink it below what this one launches with
     cudaError_t e = I.g.dim == 3 ? cudaFuncSetAttribute(k_mg_coarse<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)I.cta_smem)
+                                                        (int)budget)
                                  : cudaFuncSetAttribute(k_mg_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                        (int)I.cta_smem);
+                                                        (int)budget);
     if (e != cudaSuccess) return OSCAR_E_CUDA;
     // mixed path, opt-in (OSCAR_CLUSTER=1): the levels between the per-level
     // kernels and the coarse CTA go to the cluster kernel when they split
@@ -847,7 +850,7 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
             if (sm == (size_t)-1 || sm > budget) continue;
             void (*kern)(SLevels<T>) = I.g.dim == 3 ? k_mg_cluster<3, T> : k_mg_cluster<2, T>;
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) != cudaSuccess) {
                 cudaGetLastError();
                 break;
             }

@@ -279,6 +279,35 @@ def test_serving_results_match_alone():
         assert rec.done >= rec.admitted >= rec.arrival
 
 
+def test_instances_of_different_sizes_do_not_interfere():
+    """Creating a small instance while a larger one is in use must not change
+    the larger one's results (kernel attributes are process-wide)."""
+    big = inputs.random_small_case(9, 64, 32, nz=32, dim=3)
+    small = inputs.random_small_case(10, 12, 8)
+    pb = dict(big.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
+    ps = dict(small.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
+    dt_b = ox.oscar_timesteps(pb, 0.02)[1]
+
+    def steps(g):
+        g.drag_step(3 * 0.99 * dt_b, strict=False)
+        rc, kf, _ = g.relax(0.99 * dt_b, 3, strict=False)
+        return rc, kf
+
+    ref = ox.Oscar(pb, big.solid, big.alpha0)
+    r_ref = steps(ref)
+    a_ref = ref.field(ox.FIELD_P)
+    ref.close()
+    g = ox.Oscar(pb, big.solid, big.alpha0)
+    g.drag_step(3 * 0.99 * dt_b, strict=False)      # graphs of the big instance exist
+    h = ox.Oscar(ps, small.solid, small.alpha0)     # then a small one is created
+    h.drag_step(3 * 0.99 * dt_b, strict=False)
+    rc, kf, _ = g.relax(0.99 * dt_b, 3, strict=False)
+    assert (rc, kf) == r_ref
+    assert np.array_equal(g.field(ox.FIELD_P), a_ref)
+    g.close()
+    h.close()
+
+
 def test_edge_cases():
     # all-solid grid is rejected; a single fluid column works
     c = inputs.random_small_case(6, 5, 4)
