@@ -768,50 +768,63 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
     T rho = mix(al, fl.rho1, fl.rho2), mu = mix(al, fl.mu1, fl.mu2);
     T rAc = rA[c];
     const T Vc = GA<T>::V(g);
+    T lap[3] = {T(0), T(0), T(0)}, conv[3] = {T(0), T(0), T(0)}, tr[3] = {T(0), T(0), T(0)},
+      inflow[3] = {T(0), T(0), T(0)};
+    T vc[3];
 #pragma unroll
-    for (int comp = 0; comp < DIM; ++comp) {
-        T vc = v.a[comp][c];
-        T vin = comp == 0 ? vin0 : T(0);
-        T Hc = rho * vold.a[comp][c] / dt;
-        T lap = T(0), conv = T(0), tr = T(0), inflow = T(0);
+    for (int comp = 0; comp < DIM; ++comp) vc[comp] = v.a[comp][c];
+    // faces outer, components inner: the face type, neighbour, flux, face
+    // viscosity and upwind cell are worked out once per face
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            int off = noff(g, a);
-            T Sa = GA<T>::S(g, a), ha = GA<T>::h(g, a);
+    for (int a = 0; a < DIM; ++a) {
+        const int off = noff(g, a);
+        const T Sa = GA<T>::S(g, a), ha = GA<T>::h(g, a);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                int t = ftype(inf, a, s);
-                T sg = s ? T(1) : T(-1);
-                int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
-                if (t == FT_INTERIOR) {
-                    int nb = s ? c + off : c - off;
-                    T mun = mix(alpha[nb], fl.mu1, fl.mu2);
-                    T muf = T(0.5) * (mu + mun);
-                    lap += muf * Sa / ha * v.a[comp][nb];
-                    int L = s ? c : nb, Hh = s ? nb : c;
-                    T pc = phic.a[a][f];
-                    T vf, vu;
-                    if (pc >= T(0)) { vu = v.a[comp][L]; vf = vu + T(0.5) * ha * Gr[comp][a][L]; }
-                    else { vu = v.a[comp][Hh]; vf = vu - T(0.5) * ha * Gr[comp][a][Hh]; }
-                    T fo = sg * pc;
-                    if (fo < T(0)) inflow += -fo * v.a[comp][nb];
-                    conv += fo * (vf - vu);
-                    T dvdx = T(0.5) * (Gr[a][comp][c] + Gr[a][comp][nb]);
-                    tr += sg * muf * Sa * dvdx;
-                } else if (t == FT_WALL) {
-                    tr += sg * mu * Sa * Gr[a][comp][c];
-                } else if (t == FT_INLET) {
-                    lap += mu * Sa / (T(0.5) * ha) * vin;
-                    T fo = sg * phic.a[a][f];
-                    if (fo < T(0)) inflow += -fo * vin;
-                    else conv += fo * (vin - vc);
-                    tr += sg * mu * Sa * Gr[a][comp][c];
-                } else if (t == FT_OUTLET) {
-                    tr += sg * mu * Sa * Gr[a][comp][c];
+        for (int s = 0; s < 2; ++s) {
+            const int t = ftype(inf, a, s);
+            const T sg = s ? T(1) : T(-1);
+            const int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
+            if (t == FT_INTERIOR) {
+                const int nb = s ? c + off : c - off;
+                const T mun = mix(alpha[nb], fl.mu1, fl.mu2);
+                const T muf = T(0.5) * (mu + mun);
+                const T lapc = muf * Sa / ha;
+                const T pc = phic.a[a][f];
+                const bool fromL = pc >= T(0);
+                const int up = fromL ? (s ? c : nb) : (s ? nb : c);
+                const T hs = fromL ? T(0.5) * ha : -(T(0.5) * ha);
+                const T fo = sg * pc;
+                const T trc = sg * muf * Sa;
+#pragma unroll
+                for (int comp = 0; comp < DIM; ++comp) {
+                    const T vn = v.a[comp][nb];
+                    lap[comp] += lapc * vn;
+                    const T vu = fromL ? (s ? vc[comp] : vn) : (s ? vn : vc[comp]);
+                    const T vf = vu + hs * Gr[comp][a][up];
+                    if (fo < T(0)) inflow[comp] += -fo * vn;
+                    conv[comp] += fo * (vf - vu);
+                    tr[comp] += trc * (T(0.5) * (Gr[a][comp][c] + Gr[a][comp][nb]));
+                }
+            } else if (t == FT_WALL || t == FT_OUTLET) {
+#pragma unroll
+                for (int comp = 0; comp < DIM; ++comp) tr[comp] += sg * mu * Sa * Gr[a][comp][c];
+            } else if (t == FT_INLET) {
+                const T fo = sg * phic.a[a][f];
+#pragma unroll
+                for (int comp = 0; comp < DIM; ++comp) {
+                    const T vin = comp == 0 ? vin0 : T(0);
+                    lap[comp] += mu * Sa / (T(0.5) * ha) * vin;
+                    if (fo < T(0)) inflow[comp] += -fo * vin;
+                    else conv[comp] += fo * (vin - vc[comp]);
+                    tr[comp] += sg * mu * Sa * Gr[a][comp][c];
                 }
             }
         }
-        Hc += (lap + rho * (inflow - conv) + tr) / Vc;
+    }
+#pragma unroll
+    for (int comp = 0; comp < DIM; ++comp) {
+        T Hc = rho * vold.a[comp][c] / dt;
+        Hc += (lap[comp] + rho * (inflow[comp] - conv[comp]) + tr[comp]) / Vc;
         hbya.a[comp][c] = rAc * Hc;
     }
 }
