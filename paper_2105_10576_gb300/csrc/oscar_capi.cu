@@ -173,6 +173,7 @@ static void carve(Instance &I, Carver &C) {
         L.res = C.take(n * es);
     }
     I.stage_dev = (double *)C.take(I.stage_len * sizeof(double));
+    I.cta_img = C.take(kCtaImageBytes);
     I.partials = (double *)C.take((size_t)kRedSlots * I.red_stride * sizeof(double));
     I.scal = (double *)C.take(S_COUNT * sizeof(double));
     I.ctl = (int *)C.take(C_COUNT * sizeof(int));

@@ -14,6 +14,7 @@ constexpr int kMaxLevels = 24;
 constexpr int kRedBlocks = 1216;      // 152 SMs x 8: fixed grid of every reduction (deterministic order)
 constexpr int kRedSlots = 16;         // partial-sum slots
 constexpr double kSyncTimeoutSec = 600.0;
+constexpr size_t kCtaImageBytes = 224 * 1024;   // shared-memory budget of the coarse CTA
 
 // Scalar slots in the device scalar array (double).
 enum Slot {
@@ -101,6 +102,7 @@ struct Instance {
     int red_stride;        // partials per slot: max(kRedBlocks, blocks of a cell launch)
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     size_t cta_smem;       // shared memory of the coarse kernel
+    void *cta_img;         // shared-memory image of the coarse levels (kCtaImageBytes, built per PISO set-up)
     int lA;                // first level of the cluster kernel (mixed path), -1 when it is not used
     int pending;           // kind (0 drag, 1 relax, 2 standard) of a launched step not yet waited for, or -1
     double pending_dt;

@@ -1844,11 +1844,30 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
     __syncthreads();
 }
 
+// The shared-memory image of the coarse levels (cta_prepare with x = 0 and
+// b = 0), built once per set of coefficients (once per PISO set-up) and stored
+// in global memory, so that every V-cycle starts from one contiguous copy
+// instead of redoing the loads and the per-cell rearrangement.
 template <int DIM, typename M>
-__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P) {
+__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P, uint4 *__restrict__ img, int n16) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char sm[];
-    cta_prepare<DIM, M>(P, sm, true);
+    cta_prepare<DIM, M>(P, sm, false);
+    __syncthreads();
+    for (int q = threadIdx.x; q < n16; q += blockDim.x) img[q] = reinterpret_cast<const uint4 *>(sm)[q];
+}
+
+// The coarse V-cycle: the image (fixed during a solve) is copied in before the
+// grid-dependency wait, then b of the top level, written by the preceding
+// restriction, after it.
+template <int DIM, typename M>
+__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P, const uint4 *__restrict__ img, int n16) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    for (int q = threadIdx.x; q < n16; q += blockDim.x) reinterpret_cast<uint4 *>(sm)[q] = img[q];
+    griddep_wait();
+    M *bt = (M *)(sm + P.L[0].ob);
+    for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) bt[q] = P.b_top[q];
+    __syncthreads();
     cta_vcycle<DIM, M>(P, sm);
     for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) P.x_top[q] = ((const M *)(sm + P.L[0].ox))[q];
 }

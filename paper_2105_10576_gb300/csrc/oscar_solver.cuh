@@ -268,6 +268,12 @@ template <typename T> struct Impl {
             launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag,
                     (M *)L.idiag), ++I.nlaunch;
         }
+        if (I.lA <= 0) {   // the coarse CTA's shared-memory image for this set of coefficients
+            CLevels<M> P;
+            cta_levels(I, P, I.lc0);
+            launchk(k_mg_coarse_pack<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (uint4 *)I.cta_img,
+                    (int)(I.cta_smem / 16)), ++I.nlaunch;
+        }
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
@@ -437,7 +443,8 @@ template <typename T> struct Impl {
             cta_levels(I, P, I.lc0);
             P.b_top = lb(I, I.lc0, r);
             P.x_top = lx(I, I.lc0, z);
-            launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P), ++I.nlaunch;
+            launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (const uint4 *)I.cta_img,
+                    (int)(I.cta_smem / 16)), ++I.nlaunch;
         }
         for (int l = lk - 1; l >= 0; --l) {
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -818,7 +825,7 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
     // larger levels ran faster as separate launches) whose subtree fits the
     // shared-memory budget; OSCAR_CTA_CELLS moves the cap, for tuning
     CLevels<T> P;
-    const size_t budget = 224 * 1024;
+    const size_t budget = kCtaImageBytes;
     long long cap = 1024;
     if (const char *e = getenv("OSCAR_CTA_CELLS")) cap = atoll(e) > 0 ? atoll(e) : cap;
     I.lc0 = I.nlev - 1;
@@ -832,6 +839,11 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                                                         (int)budget)
                                  : cudaFuncSetAttribute(k_mg_coarse<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                         (int)budget);
+    if (e == cudaSuccess)
+        e = I.g.dim == 3 ? cudaFuncSetAttribute(k_mg_coarse_pack<3, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)budget)
+                         : cudaFuncSetAttribute(k_mg_coarse_pack<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)budget);
     if (e != cudaSuccess) return OSCAR_E_CUDA;
     // mixed path, opt-in (OSCAR_CLUSTER=1): the levels between the per-level
     // kernels and the coarse CTA go to the cluster kernel when they split
