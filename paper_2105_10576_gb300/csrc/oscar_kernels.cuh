@@ -1606,6 +1606,7 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
 // red-black, post-smoothing black-red, symmetric sweeps on the coarsest
 // level); the residual for the restriction is formed cell-parallel first.
 constexpr int kCtaThreads = 1024;
+constexpr int kExactCells = 128;   // coarsest CTA level solved exactly when at most this size
 template <typename M> struct CLevel {
     GridD g;
     const M *c[3];          // global face coefficients
@@ -1621,6 +1622,10 @@ template <typename M> struct CLevel {
 template <typename M> struct CLevels {
     int n, nu, nu_top, coarse_sweeps;
     int ors;           // residual scratch (cells of the largest level)
+    // exact = 1: the coarsest level (at most kExactCells cells) is solved with
+    // its explicit inverse, stored row-major at oinv (built by
+    // k_mg_coarse_pack), with chunk partial sums at opart
+    int exact, oinv, opart, nchunk;
     const M *b_top;    // global b of the top level
     M *x_top;          // global x of the top level
     CLevel<M> L[kMaxCL];
@@ -1809,13 +1814,35 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
         }
     }
     const CLevel<M> &Lc = P.L[P.n - 1];
-    for (int s = 0; s < P.coarse_sweeps; ++s) {
-        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
-        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
-    }
-    for (int s = 0; s < P.coarse_sweeps; ++s) {
-        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
-        phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
+    if (P.exact) {   // x = A^-1 b on the coarsest level: chunked dense product, then the chunk sums
+        const int ne = Lc.g.ncell, per = (ne + P.nchunk - 1) / P.nchunk;
+        const M *inv = (const M *)(sm + P.oinv), *bc = (const M *)(sm + Lc.ob);
+        M *part = (M *)(sm + P.opart);
+        __syncthreads();
+        for (int q = t; q < ne * P.nchunk; q += nt) {
+            const int row = q % ne, ch = q / ne;
+            const int j0 = ch * per, j1 = min(ne, j0 + per);
+            M acc = M(0);
+            for (int jj = j0; jj < j1; ++jj) acc += inv[row * ne + jj] * bc[jj];
+            part[ch * ne + row] = acc;
+        }
+        __syncthreads();
+        M *xc = (M *)(sm + Lc.ox);
+        for (int q = t; q < ne; q += nt) {
+            M acc = M(0);
+            for (int ch = 0; ch < P.nchunk; ++ch) acc += part[ch * ne + q];
+            xc[q] = acc;
+        }
+        prev_blk = true;   // the next phase starts with a block barrier
+    } else {
+        for (int s = 0; s < P.coarse_sweeps; ++s) {
+            phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
+            phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
+        }
+        for (int s = 0; s < P.coarse_sweeps; ++s) {
+            phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 1, t0, st);
+            phase(Lc); if (active) cta_sweep<DIM, M>(Lc, sm, 0, t0, st);
+        }
     }
     for (int l = P.n - 2; l >= 0; --l) {
         const CLevel<M> &L = P.L[l];
@@ -1848,12 +1875,70 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
 // b = 0), built once per set of coefficients (once per PISO set-up) and stored
 // in global memory, so that every V-cycle starts from one contiguous copy
 // instead of redoing the loads and the per-cell rearrangement.
+// With P.exact, the pack also forms the coarsest level's matrix (diagonal d,
+// off-diagonals -w from its per-cell form; rows of cells that are solid or
+// have no coefficients decouple) and inverts it in place by Gauss-Jordan
+// elimination without pivoting (the matrix is symmetric positive definite: the
+// fluid is connected to the Dirichlet outlet); a pivot that vanishes (a
+// fluid pocket cut off from the outlet, whose block is singular) drops its row
+// and column.
 template <int DIM, typename M>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P, uint4 *__restrict__ img, int n16) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char sm[];
     cta_prepare<DIM, M>(P, sm, false);
     __syncthreads();
+    if (P.exact) {
+        const CLevel<M> &Lc = P.L[P.n - 1];
+        const int ne = Lc.g.ncell, t = threadIdx.x, nt = blockDim.x;
+        M *A = (M *)(sm + P.oinv);
+        const M *d = (const M *)(sm + Lc.od), *w = (const M *)(sm + Lc.ow);
+        const uint32_t *pk = (const uint32_t *)(sm + Lc.opk);
+        const int nx = Lc.g.nx, nxy = Lc.g.nx * Lc.g.ny;
+        for (int q = t; q < ne * ne; q += nt) A[q] = M(0);
+        __syncthreads();
+        for (int c = t; c < ne; c += nt) {
+            const bool live = (pk[c] & kPkFluid) && d[c] > M(0);
+            A[c * ne + c] = live ? d[c] : M(0);
+            if (!live) continue;
+            const int offs[6] = {-1, 1, -nx, nx, -nxy, nxy};
+#pragma unroll
+            for (int f = 0; f < 2 * DIM; ++f) {
+                const M wf = w[2 * DIM * c + f];
+                const int nb = c + offs[f];
+                if (wf != M(0) && nb >= 0 && nb < ne) A[c * ne + nb] = -wf;
+            }
+        }
+        __shared__ M piv_s;
+        __shared__ int skip_s;
+        for (int k = 0; k < ne; ++k) {
+            __syncthreads();
+            if (t == 0) {
+                const M pv = A[k * ne + k];
+                skip_s = !(pv > M(0));
+                piv_s = skip_s ? M(0) : M(1) / pv;
+            }
+            __syncthreads();
+            const M inv = piv_s;
+            if (skip_s) {   // decoupled (or singular) row: zero row and column
+                for (int q = t; q < ne; q += nt) { A[k * ne + q] = M(0); A[q * ne + k] = M(0); }
+                continue;
+            }
+            for (int j = t; j < ne; j += nt)
+                if (j != k) A[k * ne + j] *= inv;
+            __syncthreads();
+            for (int q = t; q < ne * ne; q += nt) {
+                const int i = q / ne, j = q - i * ne;
+                if (i == k || j == k) continue;
+                A[q] -= A[i * ne + k] * A[k * ne + j];
+            }
+            __syncthreads();
+            for (int i = t; i < ne; i += nt)
+                if (i != k) A[i * ne + k] = -A[i * ne + k] * inv;
+            if (t == 0) A[k * ne + k] = inv;
+        }
+        __syncthreads();
+    }
     for (int q = threadIdx.x; q < n16; q += blockDim.x) img[q] = reinterpret_cast<const uint4 *>(sm)[q];
 }
 

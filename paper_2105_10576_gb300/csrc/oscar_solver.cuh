@@ -280,8 +280,13 @@ template <typename T> struct Impl {
 
     // levels l0.. of the single-CTA coarse kernel with their shared-memory
     // layout; returns the bytes of shared memory they need
-    static size_t cta_levels(Instance &I, CLevels<M> &P, int l0, size_t base = 0) {
+    static size_t cta_levels(Instance &I, CLevels<M> &P, int l0, size_t base = 0, bool allow_exact = true) {
         P.n = I.nlev - l0;
+        P.exact = 0;
+        P.oinv = P.opart = P.nchunk = 0;
+        if (allow_exact)   // stop at the first level small enough for an exact solve
+            for (int q = 0; q < P.n; ++q)
+                if (I.lev[l0 + q].g.ncell <= kExactCells) { P.n = q + 1; P.exact = 1; break; }
         P.nu = I.mg_nu_c;
         P.nu_top = l0 == 0 ? I.mg_nu : I.mg_nu_c;
         P.coarse_sweeps = I.mg_coarse_sweeps;
@@ -313,6 +318,12 @@ template <typename T> struct Impl {
             for (int a = 0; a < 3; ++a) C.os[a] = take(a < L.g.dim ? (size_t)L.g.nf[a] * sizeof(M) : 0);
         }
         P.ors = take(nmax * sizeof(M));
+        if (P.exact) {
+            const int ne = I.lev[l0 + P.n - 1].g.ncell;
+            P.nchunk = kCtaThreads / ne > 0 ? kCtaThreads / ne : 1;
+            P.oinv = take((size_t)ne * ne * sizeof(M));
+            P.opart = take((size_t)P.nchunk * ne * sizeof(M));
+        }
         return P.n > kMaxCL ? (size_t)-1 : off;
     }
 
@@ -351,7 +362,7 @@ template <typename T> struct Impl {
             S.oc[2] = take(L.g.dim == 3 ? (size_t)sx * L.g.ny * (L.g.nz + 1) * sizeof(M) : 0);
         }
         P.ors = take(nmax * sizeof(M));
-        size_t tot = cta_levels(I, P.C, I.lc0, off);
+        size_t tot = cta_levels(I, P.C, I.lc0, off, false);
         return P.C.n > kMaxCL ? (size_t)-1 : tot;
     }
 

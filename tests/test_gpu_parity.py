@@ -252,15 +252,16 @@ def test_batched_instances_match_alone():
 
 
 def test_serving_results_match_alone():
-    """Requests admitted while others run (staggered arrivals, a memory budget
-    that holds only some of them at once) finish with exactly the fields they
-    give when run alone, and the admission never exceeds the budget."""
+    """Requests admitted while others run (all arrive at once; the memory
+    budget holds only some of them, so the rest are admitted as the first ones
+    finish) finish with exactly the fields they give when run alone, and the
+    admission never exceeds the budget."""
     from paper_2105_10576_gb300 import serve
     cases = inputs.batched_sweep(5, seed=4, grids=((128, 16), (256, 32)))
     reqs = []
     for q, c in enumerate(cases):
         p, dtv, dtc = _batch_setup(c, 4)
-        reqs.append(serve.Request(q, 0.02 * q, p, c.solid, c.alpha0, dtv, dtc, 4, 2))
+        reqs.append(serve.Request(q, 0.0, p, c.solid, c.alpha0, dtv, dtc, 4, 2))
     fps = [ox.oscar_footprint(r.params) for r in reqs]
     g = ox.Oscar(reqs[0].params, reqs[0].solid, reqs[0].alpha0)
     assert fps[0] == g.stats()["device_bytes"]     # the footprint is what create allocates
