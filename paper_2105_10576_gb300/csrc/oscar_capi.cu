@@ -295,6 +295,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.mg_nu = 2;
     I.mg_nu_c = 2;
     I.mg_coarse_sweeps = 4;
+    I.mg_nu_cta = 2;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
@@ -310,6 +311,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
         if (enu && atoi(enu) >= 1 && atoi(enu) <= 4) I.mg_nu = atoi(enu);
         const char *enc = getenv("OSCAR_MG_NUC");
         if (enc && atoi(enc) >= 1 && atoi(enc) <= 4) I.mg_nu_c = atoi(enc);
+        const char *ect = getenv("OSCAR_MG_NU_CTA");
+        if (ect && atoi(ect) >= 1 && atoi(ect) <= 6) I.mg_nu_cta = atoi(ect);
     }
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];

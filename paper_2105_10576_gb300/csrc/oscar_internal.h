@@ -122,6 +122,7 @@ struct Instance {
     int cg_iters_last;
     long long cell_updates;
     int mg_nu, mg_nu_c, mg_coarse_sweeps;   // sweeps on the finest level, on coarser levels, on the coarsest
+    int mg_nu_cta;         // sweeps on the levels held by the coarse CTA
     long long nlaunch;     // kernel launches issued by the host (eager or into a capture)
     long long nexec;       // kernels executed on the device (graph executions counted by loop trips)
     Profiler *prof;

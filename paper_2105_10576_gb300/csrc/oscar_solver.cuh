@@ -287,8 +287,8 @@ template <typename T> struct Impl {
         if (allow_exact)   // stop at the first level small enough for an exact solve
             for (int q = 0; q < P.n; ++q)
                 if (I.lev[l0 + q].g.ncell <= kExactCells) { P.n = q + 1; P.exact = 1; break; }
-        P.nu = I.mg_nu_c;
-        P.nu_top = l0 == 0 ? I.mg_nu : I.mg_nu_c;
+        P.nu = I.mg_nu_cta;
+        P.nu_top = l0 == 0 ? I.mg_nu : I.mg_nu_cta;
         P.coarse_sweeps = I.mg_coarse_sweeps;
         size_t off = base;
         auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
