@@ -201,6 +201,20 @@ def oracle_sample(c, nx_crop: int, n_sub: int):
     return nfl * (1 + n_sub), dt, nfl, desc
 
 
+def reduce_over_ranks(dist, values_max, values_sum, device="cpu"):
+    """Max over ranks of values_max and sum over ranks of values_sum (lists of
+    floats): the job's time is its slowest replica's, its work the replicas'
+    total. `device` is "cuda" under NCCL, "cpu" under gloo."""
+    import torch
+    tm = torch.tensor(list(values_max), dtype=torch.float64, device=device)
+    ts = torch.tensor(list(values_sum), dtype=torch.float64, device=device)
+    if len(values_max):
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    if len(values_sum):
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return [float(x) for x in tm.tolist()], [float(x) for x in ts.tolist()]
+
+
 def run_reference(args, c, desc):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -482,11 +496,8 @@ def main():
     cg_its = s_after["cg_iters_total"] - s_before["cg_iters_total"]
     subs = sum(kfs)
     if dist is not None:
-        t = torch.tensor([ms, float(cu), float(launches)], device="cuda", dtype=torch.float64)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms, cu, launches = float(tmax[0]), float(t[1]), int(t[2])
+        (ms,), (cu, launches) = reduce_over_ranks(dist, [ms], [float(cu), float(launches)], "cuda")
+        launches = int(launches)
     value = cu / (ms / 1e3)
 
     # ---- roofline: each profiled kernel class timed with CUDA events on the
@@ -495,7 +506,10 @@ def main():
     es = 8 if p["precision"] == inputs.PREC_FP64 else 4
     n_piso = p["n_piso"]
     steps_total = args.steps * 1 + subs                  # drag steps + sub-steps
-    per_class_launches = {0: 4 * 2 * cg_its,              # nu=2 pre + 2 post sweeps, 2 colours, finest level
+    # finest-level half sweeps per PCG iteration: 2 nu (pre) + 2 nu (post) - 1
+    # (the first is done by the kernel producing r), counting the variants with
+    # the prolongation and r.z folded in
+    per_class_launches = {0: 7 * cg_its,
                           1: cg_its, 4: cg_its,
                           2: n_piso * steps_total, 3: steps_total}
     prof = {}
@@ -540,10 +554,8 @@ def main():
         cu_e2e = sim.stats()["cell_updates"] - cu0
         e2e = {"value": cu_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         if dist is not None:
-            t = torch.tensor([t_e2e, float(cu_e2e)], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-            e2e["value"] = float(t[1]) / float(t[0])
+            (t_max,), (cu_sum,) = reduce_over_ranks(dist, [t_e2e], [float(cu_e2e)], "cuda")
+            e2e["value"] = cu_sum / t_max
 
     tts = None
     if rank == 0 and not args.no_tts:
