@@ -54,7 +54,8 @@ def make_workload(name: str):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per launch of the profiled kernel classes
+# algorithmic bytes per launch of the profiled kernel classes (compulsory traffic:
+# each operand read or written once per launch)
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(kid: int, c, es: int) -> float:
     p = c.params
