@@ -99,16 +99,23 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the handle */
     long long kernel_launches; /* CUDA kernels launched by this handle since creation */
     int mg_first_cta_level;   /* first multigrid level held in one CTA's shared memory */
-    int mg_first_cluster_level; /* first level of the thread-block-cluster kernel, -1 when unused */
 } oscar_stats_t;
 
 typedef struct oscar_instance *oscar_handle;
 
 /* Time-step control (Section 2.2, CFL and Brackbill limits; Section 3.2, N).
- * out[0] = dt_CFL = hx / U_inlet; out[1] = dt_B = sqrt(rho_bar h_min^3 / (2 pi sigma)),
+ * out[0] = dt_CFL = hx / u; out[1] = dt_B = sqrt(rho_bar h_min^3 / (2 pi sigma)),
  * rho_bar = (rho1 + rho2)/2, h_min the smallest spacing; out[2] = dt_vd = c_cfl dt_CFL;
- * out[3] = N, the smallest integer with dt_vd / N < dt_B. Host arithmetic only. */
-int oscar_timesteps(const oscar_params *p, double c_cfl, double out[4]);
+ * out[3] = N, the smallest integer with dt_vd / N < dt_B.
+ * u is the flow velocity of the CFL condition, fixed before the run from the
+ * geometry: the injected flux U_inlet A(inlet) crosses every x cross-section,
+ * so u = U_inlet A(inlet) / min_x A(x), A(x) = fluid cells of the column
+ * i = const (the mean speed through the narrowest section; U_inlet in a
+ * straight channel). solid: host uint8[ncell] (1 = solid), or NULL for a
+ * grid without solid cells (u = U_inlet). Returns OSCAR_E_INVALID_ARG for
+ * U_inlet, sigma or c_cfl not positive, or when the inlet column has fluid
+ * but some column has none (no path to the outlet). Host arithmetic only. */
+int oscar_timesteps(const oscar_params *p, const uint8_t *solid, double c_cfl, double out[4]);
 
 /* Create an instance. solid: host uint8[ncell]; alpha0: host double[ncell]
  * (values in solid cells ignored). stream: a cudaStream_t, or NULL for a
@@ -191,27 +198,26 @@ int oscar_destroy(oscar_handle h);
 /* Static string for a return code. */
 const char *oscar_strerror(int code);
 
-/* Kernel-class timing with CUDA events on the handle's stream (measurement
- * support, not part of the method). enable = 1 starts recording every eager
- * launch of the classes below (the step calls run as captured graphs, whose
- * loop bodies hold no event nodes, so they are not recorded), 0 stops. oscar_profile_read waits for the stream
- * and returns, for class kid, the summed device time [ms] and the number of
- * launches recorded since the last reset; reset = 1 clears all classes. */
-#define OSCAR_KID_RBGS0 0      /* red-black Gauss-Seidel half-sweep, finest level */
-#define OSCAR_KID_CG_APPLY 1   /* pressure operator apply fused with p.Ap */
-#define OSCAR_KID_MOMENTUM 2   /* HbyA evaluation */
-#define OSCAR_KID_TRANSPORT 3  /* the three alpha-transport kernels of one step */
-#define OSCAR_KID_RESID0 4     /* multigrid residual, finest level */
-#define OSCAR_KID_COUNT 5
+/* In-step kernel timing (measurement support, not part of the method).
+ * enable = 1 clears any previous recording and makes the following step calls
+ * run their launch sequence eagerly (host-driven loops with one control-word
+ * read-back per loop trip, instead of the captured graphs), with a pair of
+ * CUDA events on the handle's stream around every kernel launch; the device
+ * times are accumulated per (kernel function, launch grid size), so that a
+ * multigrid kernel on two levels gives two entries. enable = 0 stops and keeps
+ * the recording. The numerics of a profiled step are those of the graph step
+ * (same kernels in the same order). Errors: OSCAR_E_INVALID_ARG while an
+ * asynchronous step is pending; OSCAR_E_CUDA if events cannot be created. */
 int oscar_profile(oscar_handle h, int enable);
-int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset);
 
-/* Launch kernel class kid reps times back to back on the current state of the
- * instance (outside any graph; the kernels write only scratch buffers, so the
- * state is unchanged) and return the mean device time per launch [ms], timed
- * with CUDA events on the handle's stream. The class TRANSPORT counts its
- * three kernels as one launch. Waits for the stream. */
-int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms);
+/* Entry `index` of the recording: *count_out (may be NULL) receives the number
+ * of entries; name_out (may be NULL) receives up to name_cap - 1 characters of
+ * the kernel's (mangled) name; grid_out the blocks of its launches; total_ms the
+ * summed device time [ms]; launches the number of timed launches. Waits for
+ * the handle's stream. Returns OSCAR_E_INVALID_ARG when index >= the count
+ * (count_out is still written). */
+int oscar_profile_read(oscar_handle h, int index, int *count_out, char *name_out, size_t name_cap,
+                       unsigned *grid_out, double *total_ms, long long *launches);
 
 /* Phase volume sum over fluid cells of alpha * cell_volume, computed without
  * allocating any device memory. The paper has no counterpart: this is a
@@ -225,9 +231,11 @@ int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms);
  *   stream      cudaStream_t of the call (NULL = default stream)
  * Scratch: a 512 KiB static device array inside the library image, held by
  * every GPU that loads the library until the process exits. The first call on
- * a device looks up that array's device address (once per device, with that
- * device current); make that first call before any stream capture. The
- * result is not waited for. Every call shares the scratch, which keeps the
+ * a device looks up that array's device address and clears it (once per
+ * device, with that device current, thread-safe; it waits for the clear on
+ * the given stream); make that first call before any stream capture. The
+ * looked-up address belongs to the device's context: do not call this again
+ * in a process after cudaDeviceReset. The result is not waited for. Every call shares the scratch, which keeps the
  * last call's contents: calls that may overlap on the GPU (different streams,
  * no ordering between them) race and must not be issued. */
 int oscar_phase_volume_noalloc(const double *alpha_dev, const uint8_t *solid_dev, long long ncell,

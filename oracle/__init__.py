@@ -78,7 +78,8 @@ def _load():
     lib.or_field.argtypes = [C.c_void_p, C.c_int, dp]
     lib.or_set_field.argtypes = [C.c_void_p, C.c_int, dp]
     lib.or_stats.argtypes = [C.c_void_p, dp]
-    lib.or_timesteps.argtypes = [pp, C.c_double, dp]
+    lib.or_timesteps.restype = C.c_int
+    lib.or_timesteps.argtypes = [pp, u8p, C.c_double, dp]
     lib.or_stage_transport.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp, dp, C.c_double, dp]
     lib.or_stage_interface.argtypes = [pp, u8p, dp, dp, dp, dp, dp, dp]
     lib.or_stage_poisson_apply.argtypes = [pp, u8p, dp, dp, dp, dp, dp]
@@ -123,12 +124,23 @@ def face_shapes(p: dict):
     return sh
 
 
-def timesteps(p: dict, c_cfl: float):
-    """(dt_cfl, dt_B, dt_vd, N) from the CFL and Brackbill limits (Section 2.2)."""
+def timesteps(p: dict, c_cfl: float, solid=None):
+    """(dt_cfl, dt_B, dt_vd, N) from the CFL and Brackbill limits (Section 2.2).
+
+    With a solid mask, the CFL velocity is the mean x velocity through the
+    narrowest cross-section, U A_inlet / A_min (mass conservation); without
+    one it is U_inlet."""
     lib = _load()
     out = np.zeros(4)
     P = make_params(p)
-    lib.or_timesteps(C.byref(P), c_cfl, _dp(out))
+    sp = None
+    if solid is not None:
+        s = np.ascontiguousarray(solid, dtype=np.uint8)
+        assert s.size == p["nx"] * p["ny"] * (p["nz"] if p["dim"] == 3 else 1)
+        sp = _u8(s)
+    rc = lib.or_timesteps(C.byref(P), sp, c_cfl, _dp(out))
+    if rc != 0:
+        raise ValueError("no fluid path from the inlet to the outlet")
     return out[0], out[1], out[2], int(out[3])
 
 

@@ -172,17 +172,44 @@ static double mix_mu(const or_params *P, double al) { return al * P->mu1 + (1.0 
 /* ------------------------------------------------------------------------- */
 /* Section 2.2: CFL and Brackbill limits; Section 3.2: N sub-steps            */
 /* out[0]=dt_cfl, out[1]=dt_B, out[2]=dt_vd, out[3]=N                         */
+/*                                                                           */
+/* The CFL limit is Delta x / u with u the flow velocity. For a constant time */
+/* step fixed before the run, u is taken as the largest cross-section mean of */
+/* the x velocity that mass conservation fixes: the injected flux U A_in      */
+/* passes every cross-section x = const, so its mean speed there is           */
+/* U A_in / A(x), largest at the narrowest section. A(x) counts the fluid     */
+/* cells of column i (all j, k). solid = NULL is an open channel (u = U).     */
+/* Returns -1 when some column has no fluid cell while the inlet has one (no  */
+/* path from the inlet to the outlet), else 0.                                */
 /* ------------------------------------------------------------------------- */
-void or_timesteps(const or_params *P, double c_cfl, double *out) {
+int or_timesteps(const or_params *P, const uint8_t *solid, double c_cfl, double *out) {
     double hmin = P->hx;
     if (P->hy < hmin) hmin = P->hy;
     if (P->dim == 3 && P->hz < hmin) hmin = P->hz;
-    double dt_cfl = P->hx / P->U_inlet;                 /* Delta x / u, flow along x */
+    double u = P->U_inlet;
+    if (solid) {
+        int nz = P->dim == 3 ? P->nz : 1;
+        long a_in = -1, a_min = -1;
+        for (int i = 0; i < P->nx; ++i) {
+            long a = 0;
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < P->ny; ++j)
+                    if (solid[i + P->nx * (j + P->ny * k)] == 0) a += 1;
+            if (i == 0) a_in = a;
+            if (a_min < 0 || a < a_min) a_min = a;
+        }
+        if (a_in > 0) {
+            if (a_min == 0) return -1;
+            u = P->U_inlet * (double)a_in / (double)a_min;
+        }
+    }
+    double dt_cfl = P->hx / u;                           /* Delta x / u, flow along x */
     double rho_bar = 0.5 * (P->rho1 + P->rho2);          /* average density of the two phases */
     double dt_b = sqrt(rho_bar * hmin * hmin * hmin / (2.0 * M_PI * P->sigma));
     double dt_vd = c_cfl * dt_cfl;
     double N = floor(dt_vd / dt_b) + 1.0;                /* smallest integer with dt_vd/N < dt_B */
     out[0] = dt_cfl; out[1] = dt_b; out[2] = dt_vd; out[3] = N;
+    return 0;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -7,8 +7,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cxxabi.h>
+
 #include <chrono>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "oscar_internal.h"
@@ -35,32 +38,46 @@ int sync_bounded(cudaStream_t s, double timeout_sec) {
     }
 }
 
-int prof_begin(Instance &I, int kid) {
-    Profiler *P = I.prof;
-    if (!P || !P->enabled || I.capturing) return -1;   // no event nodes inside captured graphs
-    if (P->n >= kProfPool) {
-        // drain: wait for the recorded launches and accumulate their times
-        if (sync_bounded(I.stream, kSyncTimeoutSec)) { P->dropped++; return -1; }
-        for (int s = 0; s < P->n; ++s) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, P->ev0[s], P->ev1[s]) == cudaSuccess) {
-                P->total_ms[P->kid[s]] += ms;
-                P->launches[P->kid[s]] += 1;
-            } else {
-                cudaGetLastError();
-                P->dropped++;
-            }
+// accumulate the recorded event pairs into their entries (waits for st)
+int prof_drain(Profiler *P, cudaStream_t st) {
+    if (P->n == 0) return 0;
+    int rc = sync_bounded(st, kSyncTimeoutSec);
+    for (int s = 0; s < P->n; ++s) {
+        float ms = 0.f;
+        if (!rc && cudaEventElapsedTime(&ms, P->ev0[s], P->ev1[s]) == cudaSuccess) {
+            P->ent[P->slot_entry[s]].total_ms += ms;
+            P->ent[P->slot_entry[s]].launches += 1;
+        } else {
+            cudaGetLastError();
+            P->dropped++;
         }
-        P->n = 0;
     }
+    P->n = 0;
+    return rc;
+}
+
+int prof_begin(Profiler *P, cudaStream_t st, const void *fn, dim3 grid, dim3 block) {
+    const unsigned gsz = grid.x * grid.y * grid.z, bsz = block.x * block.y * block.z;
+    int e = 0;
+    while (e < P->nent && !(P->ent[e].fn == fn && P->ent[e].grid == gsz && P->ent[e].block == bsz)) ++e;
+    if (e == P->nent) {
+        if (P->nent >= kProfKinds) { P->dropped++; return -1; }
+        P->ent[e].fn = fn;
+        P->ent[e].grid = gsz;
+        P->ent[e].block = bsz;
+        P->ent[e].total_ms = 0.0;
+        P->ent[e].launches = 0;
+        P->nent++;
+    }
+    if (P->n >= kProfPool && prof_drain(P, st)) { P->dropped++; return -1; }
     int s = P->n++;
-    P->kid[s] = kid;
-    cudaEventRecord(P->ev0[s], I.stream);
+    P->slot_entry[s] = e;
+    cudaEventRecord(P->ev0[s], st);
     return s;
 }
 
-void prof_end(Instance &I, int slot) {
-    if (slot >= 0) cudaEventRecord(I.prof->ev1[slot], I.stream);
+void prof_end(Profiler *P, cudaStream_t st, int slot) {
+    if (slot >= 0) cudaEventRecord(P->ev1[slot], st);
 }
 
 size_t field_len(const Instance &I, int which) {
@@ -201,12 +218,30 @@ using namespace oscar;
 
 extern "C" {
 
-int oscar_timesteps(const oscar_params *p, double c_cfl, double out[4]) {
+int oscar_timesteps(const oscar_params *p, const uint8_t *solid, double c_cfl, double out[4]) {
     if (!p || !out || !(p->U_inlet > 0) || !(p->sigma > 0) || !(c_cfl > 0)) return OSCAR_E_INVALID_ARG;
+    if (p->nx < 1 || p->ny < 1 || (p->dim == 3 && p->nz < 1)) return OSCAR_E_INVALID_ARG;
     double hmin = p->hx;
     if (p->hy < hmin) hmin = p->hy;
     if (p->dim == 3 && p->hz < hmin) hmin = p->hz;
-    double dt_cfl = p->hx / p->U_inlet;
+    // CFL velocity: the injected flux U A(inlet) crosses every x-section, so
+    // the largest section-mean speed is U A(inlet) / min_x A(x)
+    double u_cfl = p->U_inlet;
+    if (solid) {
+        const long long nyz = (long long)p->ny * (p->dim == 3 ? p->nz : 1);
+        std::vector<long long> area(p->nx, 0);
+        for (long long r = 0; r < nyz; ++r) {
+            const uint8_t *row = solid + r * p->nx;
+            for (int i = 0; i < p->nx; ++i) area[i] += row[i] == 0;
+        }
+        long long amin = area[0];
+        for (int i = 1; i < p->nx; ++i) amin = area[i] < amin ? area[i] : amin;
+        if (area[0] > 0) {
+            if (amin == 0) return OSCAR_E_INVALID_ARG;   // the inlet does not reach the outlet
+            u_cfl = p->U_inlet * (double)area[0] / (double)amin;
+        }
+    }
+    double dt_cfl = p->hx / u_cfl;
     double rho_bar = 0.5 * (p->rho1 + p->rho2);
     double dt_b = sqrt(rho_bar * hmin * hmin * hmin / (2.0 * M_PI * p->sigma));
     double dt_vd = c_cfl * dt_cfl;
@@ -509,7 +544,6 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out) {
     out->device_bytes = I.arena_bytes;
     out->kernel_launches = I.nexec;
     out->mg_first_cta_level = I.lc0;
-    out->mg_first_cluster_level = I.lA;
     return 0;
 }
 
@@ -526,53 +560,74 @@ int oscar_profile(oscar_handle h, int enable) {
         if (!I.prof) return OSCAR_E_OOM;
         memset(I.prof, 0, sizeof(Profiler));
     }
-    if (enable && !I.prof->created) {
+    Profiler *P = I.prof;
+    if (enable && !P->created) {
         for (int s = 0; s < kProfPool; ++s) {
-            if (cudaEventCreate(&I.prof->ev0[s]) != cudaSuccess || cudaEventCreate(&I.prof->ev1[s]) != cudaSuccess)
+            if (cudaEventCreate(&P->ev0[s]) != cudaSuccess || cudaEventCreate(&P->ev1[s]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int q = 0; q <= s; ++q) { cudaEventDestroy(P->ev0[q]); cudaEventDestroy(P->ev1[q]); }
                 return OSCAR_E_CUDA;
+            }
         }
-        I.prof->created = 1;
+        P->created = 1;
     }
-    I.prof->enabled = enable ? 1 : 0;
+    if (enable) {   // a new recording: clear the previous one
+        P->n = 0;
+        P->nent = 0;
+        P->dropped = 0;
+    } else if (P->created) {
+        int rc = prof_drain(P, I.stream);
+        if (rc) return rc;
+    }
+    P->enabled = enable ? 1 : 0;
     return 0;
 }
 
-int oscar_profile_kernel(oscar_handle h, int kid, int reps, double *avg_ms) {
-    if (!h || !avg_ms || reps < 1 || kid < 0 || kid >= OSCAR_KID_COUNT) return OSCAR_E_INVALID_ARG;
+int oscar_profile_read(oscar_handle h, int index, int *count_out, char *name_out, size_t name_cap,
+                       unsigned *grid_out, double *total_ms, long long *launches) {
+    if (!h || index < 0) return OSCAR_E_INVALID_ARG;
     Instance &I = h->I;
     if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
-    return I.prec == OSCAR_FP64 ? Solver<double>::profile_kernel(I, kid, reps, avg_ms)
-                                : Solver<float>::profile_kernel(I, kid, reps, avg_ms);
-}
-
-int oscar_profile_read(oscar_handle h, int kid, double *total_ms, long long *launches, int reset) {
-    if (!h || kid < 0 || kid >= OSCAR_KID_COUNT) return OSCAR_E_INVALID_ARG;
-    Instance &I = h->I;
     Profiler *P = I.prof;
-    if (!P) {
-        if (total_ms) *total_ms = 0.0;
-        if (launches) *launches = 0;
-        return 0;
+    const int n = P ? P->nent : 0;
+    if (count_out) *count_out = n;
+    if (P && P->created) {
+        int rc = prof_drain(P, I.stream);
+        if (rc) return rc;
     }
-    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
-    if (rc) return rc;
-    for (int s = 0; s < P->n; ++s) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, P->ev0[s], P->ev1[s]) == cudaSuccess) {
-            P->total_ms[P->kid[s]] += ms;
-            P->launches[P->kid[s]] += 1;
-        } else {
+    if (index >= n) return OSCAR_E_INVALID_ARG;
+    const ProfEntry &E = P->ent[index];
+    if (name_out && name_cap > 0) {
+        const char *nm = nullptr;
+        if (cudaFuncGetName(&nm, E.fn) != cudaSuccess || !nm) {
             cudaGetLastError();
-            P->dropped++;
+            nm = "?";
         }
+        // readable form: "k_name<template args>" without the namespace and parameters
+        std::string out = nm;
+        int st = 0;
+        char *dm = abi::__cxa_demangle(nm, nullptr, nullptr, &st);
+        if (st == 0 && dm) {
+            out = dm;
+            free(dm);
+            size_t lt = out.find('<'), lp = out.find('(');
+            size_t cut = lp;
+            if (lt != std::string::npos && lt < lp) {   // the parameter list follows the matching '>'
+                int depth = 0;
+                for (size_t q = lt; q < out.size(); ++q) {
+                    if (out[q] == '<') ++depth;
+                    else if (out[q] == '>' && --depth == 0) { cut = q + 1; break; }
+                }
+            }
+            if (cut != std::string::npos) out = out.substr(0, cut);
+            if (out.rfind("void ", 0) == 0) out = out.substr(5);
+            for (size_t q; (q = out.find("oscar::")) != std::string::npos;) out.erase(q, 7);
+        }
+        snprintf(name_out, name_cap, "%s", out.c_str());
     }
-    P->n = 0;
-    if (total_ms) *total_ms = P->total_ms[kid];
-    if (launches) *launches = P->launches[kid];
-    if (reset) {
-        for (int k = 0; k < OSCAR_KID_COUNT; ++k) { P->total_ms[k] = 0.0; P->launches[k] = 0; }
-        P->dropped = 0;
-    }
+    if (grid_out) *grid_out = E.grid;
+    if (total_ms) *total_ms = E.total_ms;
+    if (launches) *launches = E.launches;
     return 0;
 }
 

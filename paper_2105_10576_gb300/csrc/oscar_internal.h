@@ -51,18 +51,33 @@ struct Level {
     void *x, *b, *res;   // T
 };
 
-// Optional kernel-class timing (events recorded around selected launches).
+// In-step kernel timing: while enabled, step calls run their launch sequence
+// eagerly (host-driven loops instead of graphs) with a pair of CUDA events on
+// the launching stream around every kernel, accumulated per kernel function
+// and launch geometry (a multigrid kernel on two levels is two entries).
 constexpr int kProfPool = 8192;
+constexpr int kProfKinds = 192;
+struct ProfEntry {
+    const void *fn;
+    unsigned grid, block;
+    double total_ms;
+    long long launches;
+};
 struct Profiler {
     int enabled;
-    int n;                       // events pairs in use
-    long long dropped;
-    int kid[kProfPool];
-    cudaEvent_t ev0[kProfPool], ev1[kProfPool];
-    double total_ms[OSCAR_KID_COUNT];
-    long long launches[OSCAR_KID_COUNT];
     int created;
+    int n;                       // event pairs in use
+    long long dropped;
+    int slot_entry[kProfPool];
+    cudaEvent_t ev0[kProfPool], ev1[kProfPool];
+    int nent;
+    ProfEntry ent[kProfKinds];
 };
+// the profiler of the step being issued on this host thread (null when off)
+inline thread_local Profiler *t_prof = nullptr;
+int prof_begin(Profiler *P, cudaStream_t st, const void *fn, dim3 grid, dim3 block);
+void prof_end(Profiler *P, cudaStream_t st, int slot);
+int prof_drain(Profiler *P, cudaStream_t st);
 
 // Device memory of one instance; element type T (double or float) is fixed by
 // the precision chosen at creation. CG vectors and accumulators are double.
@@ -103,11 +118,9 @@ struct Instance {
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     size_t cta_smem;       // shared memory of the coarse kernel
     void *cta_img;         // shared-memory image of the coarse levels (kCtaImageBytes, built per PISO set-up)
-    int lA;                // first level of the cluster kernel (mixed path), -1 when it is not used
     int pending;           // kind (0 drag, 1 relax, 2 standard) of a launched step not yet waited for, or -1
     double pending_dt;
     int pending_N;
-    size_t cl_smem;        // shared memory per CTA of the cluster kernel
     unsigned *ticket;      // block counter of the single-pass reductions (0 between kernels)
     double *scal;          // S_COUNT device scalars
     double *scal_host;     // pinned mirror
@@ -141,8 +154,6 @@ struct Instance {
     int own_stream;        // the library created I.stream
 };
 
-int prof_begin(Instance &I, int kid);
-void prof_end(Instance &I, int slot);
 
 // per-precision entry points (defined in oscar_kernels.cuh, instantiated twice)
 template <typename T> struct Solver {
@@ -155,7 +166,6 @@ template <typename T> struct Solver {
     static int field_to_device(Instance &I, int which, double *dst, size_t n);
     static int field_from_device(Instance &I, int which, const double *src, size_t n);
     static int phase_volume(Instance &I, double *out);
-    static int profile_kernel(Instance &I, int kid, int reps, double *avg_ms);
     static void release_graphs(Instance &I);
 };
 

@@ -18,7 +18,6 @@
 //
 // Included by exactly one translation unit per element type.
 #pragma once
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -1955,247 +1954,6 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P, cons
     __syncthreads();
     cta_vcycle<DIM, M>(P, sm);
     for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) P.x_top[q] = ((const M *)(sm + P.L[0].ox))[q];
-}
-
-// ---------------------------------------------------------------------------
-// The middle multigrid levels in one thread-block cluster (mixed path). Each
-// of kClusterCtas CTAs holds an x-slab of every slab level in its shared
-// memory (x, b, 1/diagonal, residual scratch and the slab's face
-// coefficients); a stencil reads the neighbour slab's boundary plane through
-// distributed shared memory, and phases are separated by cluster barriers
-// instead of kernel launches. The slabs are aligned with the coarsening, so
-// restriction and prolongation stay inside a CTA, except into and out of the
-// coarse levels below, which rank 0 works as k_mg_coarse does
-// (cta_prepare / cta_vcycle) while the other CTAs wait.
-// ---------------------------------------------------------------------------
-constexpr int kClusterCtas = 16;
-constexpr int kMaxSL = 8;
-template <typename M> struct SLevel {
-    GridD g;                 // the whole level
-    int sx;                  // slab width: rank r holds x in [r sx, (r + 1) sx)
-    const M *c[3];           // global face coefficients
-    const M *idiag;          // global 1 / diagonal (0 on solid cells)
-    int r[3];                // ratios to the next level (1 or 2)
-    float rsx, rsx1, rny, rny1, rhx;   // 1/sx, 1/(sx+1), 1/ny, 1/(ny+1), 1/ceil(sx/2)
-    int ox, ob, oi, oc[3];   // shared-memory byte offsets (the same in every CTA)
-};
-template <typename M> struct SLevels {
-    int n, nu, nu_top;
-    int ors;                 // residual scratch (largest slab)
-    const M *b_top;          // global b of the top slab level
-    M *x_top;                // global x of the top slab level
-    SLevel<M> L[kMaxSL];
-    CLevels<M> C;            // the levels below, worked by rank 0
-};
-
-// sum of the neighbour terms of a slab cell, and the diagonal (sum of the
-// face coefficients, as k_mg_diag); the x-neighbours across the slab
-// boundary come from the adjacent CTAs
-template <int DIM, typename M>
-__device__ __forceinline__ M slab_off(const SLevel<M> &L, const unsigned char *sm, const M *x, const M *xprev,
-                                      const M *xnext, int x0, int il, int j, int k, int q, M &d) {
-    const int sx = L.sx, ny = L.g.ny, nz = L.g.nz, i = x0 + il;
-    const M *cx = (const M *)(sm + L.oc[0]), *cy = (const M *)(sm + L.oc[1]), *cz = (const M *)(sm + L.oc[2]);
-    const int fx = il + (sx + 1) * (j + ny * k);
-    const M wl = cx[fx], wh = cx[fx + 1];
-    M off = M(0);
-    if (i > 0) off += wl * (il > 0 ? x[q - 1] : xprev[q + sx - 1]);
-    if (i < L.g.nx - 1) off += wh * (il < sx - 1 ? x[q + 1] : xnext[q - sx + 1]);
-    const int fy = il + sx * (j + (ny + 1) * k);
-    const M yl = cy[fy], yh = cy[fy + sx];
-    if (j > 0) off += yl * x[q - sx];
-    if (j < ny - 1) off += yh * x[q + sx];
-    d = M(0);
-    d += wl + wh;
-    d += yl + yh;
-    if (DIM == 3) {
-        const M zl = cz[q], zh = cz[q + sx * ny];
-        if (k > 0) off += zl * x[q - sx * ny];
-        if (k < nz - 1) off += zh * x[q + sx * ny];
-        d += zl + zh;
-    }
-    return off;
-}
-
-template <int DIM, typename M>
-__device__ __forceinline__ void slab_sweep(const SLevel<M> &L, unsigned char *sm, const M *xprev, const M *xnext,
-                                           int x0, int colour) {
-    M *x = (M *)(sm + L.ox);
-    const M *b = (const M *)(sm + L.ob), *iv = (const M *)(sm + L.oi);
-    const int sx = L.sx, ny = L.g.ny;
-    const int hx = (sx + 1) >> 1, nh = hx * ny * L.g.nz;
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        int ti, j, k;
-        split3(h, hx, L.rhx, ny, L.rny, ti, j, k);
-        const int il = 2 * ti + ((x0 + j + k + colour) & 1);
-        if (il >= sx) continue;
-        const int q = il + sx * (j + ny * k);
-        const M id = iv[q];
-        if (id == M(0)) continue;
-        M d;
-        const M off = slab_off<DIM, M>(L, sm, x, xprev, xnext, x0, il, j, k, q, d);
-        x[q] = (b[q] + off) * id;
-    }
-}
-
-// local slab copy of a global array of a (ex, ey, ez)-shaped per-slab box
-// whose global x extent is gx (cells: gx = nx, x-faces: nx + 1)
-template <typename M>
-__device__ __forceinline__ void slab_load(M *dst, const M *src, int ex, float rex, int ey, float rey, int ez, int x0,
-                                          int gx, int gy) {
-    const int n = ex * ey * ez;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-        int a, bb, c;
-        split3(q, ex, rex, ey, rey, a, bb, c);
-        CpAsync<sizeof(M)>::copy(dst + q, src + (x0 + a) + gx * (bb + gy * c));
-    }
-}
-
-template <int DIM, typename M>
-__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_cluster(SLevels<M> P) {
-    namespace cgx = cooperative_groups;
-    cgx::cluster_group cl = cgx::this_cluster();
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int rank = (int)cl.block_rank();
-    const int t = threadIdx.x, nt = blockDim.x;
-    // 1. solve-invariant loads (coefficients, 1/diagonal; rank 0 also the
-    //    coarse levels), then b of the top slab level
-    for (int l = 0; l < P.n; ++l) {
-        const SLevel<M> &L = P.L[l];
-        const GridD &g = L.g;
-        const int sx = L.sx, x0 = rank * sx;
-        slab_load<M>((M *)(sm + L.oc[0]), L.c[0], sx + 1, L.rsx1, g.ny, L.rny, g.nz, x0, g.nx + 1, g.ny);
-        slab_load<M>((M *)(sm + L.oc[1]), L.c[1], sx, L.rsx, g.ny + 1, L.rny1, g.nz, x0, g.nx, g.ny + 1);
-        if (DIM == 3) slab_load<M>((M *)(sm + L.oc[2]), L.c[2], sx, L.rsx, g.ny, L.rny, g.nz + 1, x0, g.nx, g.ny);
-        slab_load<M>((M *)(sm + L.oi), L.idiag, sx, L.rsx, g.ny, L.rny, g.nz, x0, g.nx, g.ny);
-    }
-    if (rank == 0) cta_prepare<DIM, M>(P.C, sm, false);
-    griddep_wait();
-    {
-        const SLevel<M> &L = P.L[0];
-        slab_load<M>((M *)(sm + L.ob), P.b_top, L.sx, L.rsx, L.g.ny, L.rny, L.g.nz, rank * L.sx, L.g.nx, L.g.ny);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    {   // first colour-0 half sweep of the top slab level from x = 0
-        const SLevel<M> &L = P.L[0];
-        const int sx = L.sx, x0 = rank * sx, n = sx * L.g.ny * L.g.nz;
-        M *x = (M *)(sm + L.ox);
-        const M *b = (const M *)(sm + L.ob), *iv = (const M *)(sm + L.oi);
-        for (int q = t; q < n; q += nt) {
-            int il, j, k;
-            split3(q, sx, L.rsx, L.g.ny, L.rny, il, j, k);
-            x[q] = ((x0 + il + j + k) & 1) == 0 ? b[q] * iv[q] : M(0);
-        }
-    }
-    M *rs = (M *)(sm + P.ors);
-    // 2. down
-    for (int l = 0; l < P.n; ++l) {
-        const SLevel<M> &L = P.L[l];
-        const int sx = L.sx, x0 = rank * sx, ny = L.g.ny, nz = L.g.nz;
-        M *xl = (M *)(sm + L.ox);
-        const M *xprev = cl.map_shared_rank(xl, rank > 0 ? rank - 1 : rank);
-        const M *xnext = cl.map_shared_rank(xl, rank < kClusterCtas - 1 ? rank + 1 : rank);
-        const int nu = l == 0 ? P.nu_top : P.nu;
-        for (int s = 0; s < nu; ++s) {
-            if (s > 0) { cl.sync(); slab_sweep<DIM, M>(L, sm, xprev, xnext, x0, 0); }
-            cl.sync();
-            slab_sweep<DIM, M>(L, sm, xprev, xnext, x0, 1);
-        }
-        cl.sync();
-        {   // residual
-            const M *b = (const M *)(sm + L.ob);
-            const int n = sx * ny * nz;
-            for (int q = t; q < n; q += nt) {
-                int il, j, k;
-                split3(q, sx, L.rsx, ny, L.rny, il, j, k);
-                M d;
-                const M off = slab_off<DIM, M>(L, sm, xl, xprev, xnext, x0, il, j, k, q, d);
-                rs[q] = b[q] - (d * xl[q] - off);
-            }
-        }
-        __syncthreads();
-        {   // restriction: into the next slab level (with its first colour-0
-            // half sweep from x = 0), or into rank 0's top coarse level
-            const int rx = L.r[0], ry = L.r[1], rz = L.r[2];
-            const bool to_slab = l + 1 < P.n;
-            const GridD &gc = to_slab ? P.L[l + 1].g : P.C.L[0].g;
-            const int sxc = sx / rx, x0c = x0 / rx, nyc = gc.ny, nzc = gc.nz;
-            const int n = sxc * nyc * nzc;
-            const float rsxc = to_slab ? P.L[l + 1].rsx : 1.0f / (float)sxc;
-            const float rnyc = to_slab ? P.L[l + 1].rny : P.C.L[0].rny;
-            M *bt = to_slab ? (M *)(sm + P.L[l + 1].ob) : cl.map_shared_rank((M *)(sm + P.C.L[0].ob), 0);
-            M *xc = to_slab ? (M *)(sm + P.L[l + 1].ox) : nullptr;
-            const M *ivc = to_slab ? (const M *)(sm + P.L[l + 1].oi) : nullptr;
-            for (int q = t; q < n; q += nt) {
-                int I, J, K;
-                split3(q, sxc, rsxc, nyc, rnyc, I, J, K);
-                M acc = M(0);
-                for (int oz = 0; oz < rz; ++oz) {
-                    const int kk = K * rz + oz;
-                    if (kk >= nz) break;
-                    for (int oy = 0; oy < ry; ++oy) {
-                        const int jj = J * ry + oy;
-                        if (jj >= ny) break;
-                        for (int ox = 0; ox < rx; ++ox) acc += rs[(I * rx + ox) + sx * (jj + ny * kk)];
-                    }
-                }
-                if (to_slab) {
-                    bt[q] = acc;
-                    xc[q] = ((x0c + I + J + K) & 1) == 0 ? acc * ivc[q] : M(0);
-                } else {
-                    bt[(x0c + I) + gc.nx * (J + nyc * K)] = acc;
-                }
-            }
-        }
-    }
-    // 3. the coarse levels on rank 0
-    cl.sync();
-    if (rank == 0) cta_vcycle<DIM, M>(P.C, sm);
-    cl.sync();
-    // 4. up
-    for (int l = P.n - 1; l >= 0; --l) {
-        const SLevel<M> &L = P.L[l];
-        const int sx = L.sx, x0 = rank * sx, ny = L.g.ny, nz = L.g.nz;
-        M *xl = (M *)(sm + L.ox);
-        const M *xprev = cl.map_shared_rank(xl, rank > 0 ? rank - 1 : rank);
-        const M *xnext = cl.map_shared_rank(xl, rank < kClusterCtas - 1 ? rank + 1 : rank);
-        {   // prolongation (piecewise constant) from the next level
-            const bool from_slab = l + 1 < P.n;
-            const GridD &gc = from_slab ? P.L[l + 1].g : P.C.L[0].g;
-            const int s0 = L.r[0] >> 1, s1 = L.r[1] >> 1, s2 = L.r[2] >> 1;
-            const M *xc = from_slab ? (const M *)(sm + P.L[l + 1].ox)
-                                    : cl.map_shared_rank((const M *)(sm + P.C.L[0].ox), 0);
-            const int sxc = from_slab ? P.L[l + 1].sx : gc.nx, xoff = from_slab ? 0 : (x0 >> s0);
-            const M *iv = (const M *)(sm + L.oi);
-            const int n = sx * ny * nz;
-            for (int q = t; q < n; q += nt) {
-                if (iv[q] == M(0)) continue;
-                int il, j, k;
-                split3(q, sx, L.rsx, ny, L.rny, il, j, k);
-                xl[q] += xc[(xoff + (il >> s0)) + sxc * ((j >> s1) + gc.ny * (k >> s2))];
-            }
-        }
-        const int nu = l == 0 ? P.nu_top : P.nu;
-        for (int s = 0; s < nu; ++s) {
-            cl.sync();
-            slab_sweep<DIM, M>(L, sm, xprev, xnext, x0, 1);
-            cl.sync();
-            slab_sweep<DIM, M>(L, sm, xprev, xnext, x0, 0);
-        }
-        __syncthreads();
-    }
-    {   // x of the top slab level back to global memory
-        const SLevel<M> &L = P.L[0];
-        const int sx = L.sx, x0 = rank * sx, n = sx * L.g.ny * L.g.nz;
-        const M *xl = (const M *)(sm + L.ox);
-        for (int q = t; q < n; q += nt) {
-            int il, j, k;
-            split3(q, sx, L.rsx, L.g.ny, L.rny, il, j, k);
-            P.x_top[(x0 + il) + L.g.nx * (j + L.g.ny * k)] = xl[q];
-        }
-    }
-    cl.sync();   // no CTA leaves while others may still read its shared memory
 }
 
 }  // namespace oscar

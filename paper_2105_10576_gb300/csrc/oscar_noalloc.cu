@@ -12,6 +12,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/oscar.h"
 #include "oscar_internal.h"
 
@@ -25,9 +28,13 @@ constexpr long long kNaMaxCells = (long long)kNaBlock * kNaMaxBlocks;   // 16,77
 static __device__ __align__(256) double g_na_scratch[kNaMaxBlocks + 32];
 
 // device addresses of the scratch, one per device (host code cannot use the
-// symbol itself: on the host it only names a stand-in, not device memory)
+// symbol itself: on the host it only names a stand-in, not device memory).
+// Published once per device under g_na_mu; read without the lock afterwards.
+// A cudaDeviceReset destroys the context that the address belongs to, so the
+// entry point must not be called again in a process after a device reset.
 constexpr int kNaMaxDevices = 64;
-static double *g_na_ptr[kNaMaxDevices];
+static std::atomic<double *> g_na_ptr[kNaMaxDevices];
+static std::mutex g_na_mu;
 
 __global__ void k_na_phase_volume(const double *__restrict__ alpha, const uint8_t *__restrict__ solid, int ncell,
                                   double V, double *__restrict__ scratch, double *__restrict__ out) {
@@ -48,7 +55,9 @@ __global__ void k_na_phase_volume(const double *__restrict__ alpha, const uint8_
     }
     __syncthreads();
     if (!last) return;
-    // the block that finishes last sums the partials in block order
+    // the block that finishes last sums the partials in a fixed order (each
+    // thread a fixed strided subset, then a fixed shuffle and warp order), so
+    // the result does not depend on which block finished last
     __threadfence();
     double s = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += kNaBlock) s += __ldcg(scratch + b);
@@ -72,18 +81,30 @@ extern "C" int oscar_phase_volume_noalloc(const double *alpha_dev, const uint8_t
     if (ncell > kNaMaxCells) return OSCAR_E_INVALID_ARG;   // beyond the static scratch
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return OSCAR_E_CUDA;
-    if (!g_na_ptr[dev]) {
-        // one-time set-up on this device (must not run under stream capture)
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return OSCAR_E_CUDA;
+    double *scratch = g_na_ptr[dev].load(std::memory_order_acquire);
+    if (!scratch) {
+        // one-time set-up on this device (must not run under stream capture):
+        // look the scratch up, clear it and wait for the clear, so that no call
+        // from any thread or stream can see an uncleared block counter
+        std::lock_guard<std::mutex> lock(g_na_mu);
+        scratch = g_na_ptr[dev].load(std::memory_order_acquire);
+        if (!scratch) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return OSCAR_E_CUDA;
+            }
+            if (cudaMemsetAsync(p, 0, sizeof(g_na_scratch), (cudaStream_t)stream) != cudaSuccess ||
+                cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+                cudaGetLastError();
+                return OSCAR_E_CUDA;
+            }
+            scratch = static_cast<double *>(p);
+            g_na_ptr[dev].store(scratch, std::memory_order_release);
         }
-        if (cudaMemsetAsync(p, 0, sizeof(g_na_scratch), (cudaStream_t)stream) != cudaSuccess) return OSCAR_E_CUDA;
-        g_na_ptr[dev] = static_cast<double *>(p);
     }
     int nb = (int)((ncell + kNaBlock - 1) / kNaBlock);
     k_na_phase_volume<<<nb, kNaBlock, 0, (cudaStream_t)stream>>>(alpha_dev, solid_dev, (int)ncell, cell_volume,
-                                                                 g_na_ptr[dev], result_dev);
+                                                                 scratch, result_dev);
     return cudaGetLastError() == cudaSuccess ? 0 : OSCAR_E_CUDA;
 }

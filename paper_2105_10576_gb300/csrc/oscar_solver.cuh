@@ -49,32 +49,14 @@ inline void launchk(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    if (Profiler *P = t_prof) {   // in-step timing (eager steps only; never while capturing)
+        int slot = prof_begin(P, st, (const void *)kern, grid, block);
+        cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+        prof_end(P, st, slot);
+    } else {
+        cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+    }
 }
-
-// one cluster of kClusterCtas CTAs of kCtaThreads threads, with programmatic
-// dependent launch like launchk
-template <typename... KArgs, typename... Args>
-inline void launch_cluster(void (*kern)(KArgs...), size_t smem, cudaStream_t st, Args &&...args) {
-    cudaLaunchConfig_t cfg;
-    memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(kClusterCtas);
-    cfg.blockDim = dim3(kCtaThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = kClusterCtas;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 2;
-    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
-
-
 
 // ---------------------------------------------------------------------------
 // control kernels (one thread). The other loop decisions are taken by the
@@ -197,7 +179,6 @@ template <typename T> struct Impl {
         GridD g = to_dev(I.g);
         L3 L = launch3(I.g);
         T rV = (T)(dt / I.g.V);
-        int ps = prof_begin(I, OSCAR_KID_TRANSPORT);
         launchk(k_transport_low<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
                                                                   (T)I.P.c_alpha, (T)I.P.alpha_inlet, rV, tp(I.aL),
                                                                   tp(I.Pp), tp(I.Pm)), ++I.nlaunch;
@@ -206,7 +187,6 @@ template <typename T> struct Impl {
         launchk(k_transport_update<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, tp(I.alpha), c3(phi), c3(I.nf),
                                                                      (T)I.P.c_alpha, tp(I.aL), tp(I.Rp), tp(I.Rm), rV,
                                                                      tp(I.alpha_new)), ++I.nlaunch;
-        prof_end(I, ps);
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
@@ -268,7 +248,7 @@ template <typename T> struct Impl {
             launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag,
                     (M *)L.idiag), ++I.nlaunch;
         }
-        if (I.lA <= 0) {   // the coarse CTA's shared-memory image for this set of coefficients
+        {   // the coarse CTA's shared-memory image for this set of coefficients
             CLevels<M> P;
             cta_levels(I, P, I.lc0);
             launchk(k_mg_coarse_pack<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (uint4 *)I.cta_img,
@@ -327,45 +307,6 @@ template <typename T> struct Impl {
         return P.n > kMaxCL ? (size_t)-1 : off;
     }
 
-    // Levels lA .. lc0-1 as x-slabs of the cluster kernel, the levels below on
-    // rank 0; returns the shared memory per CTA, or (size_t)-1 when a level
-    // does not split into kClusterCtas slabs aligned with its coarsening.
-    static size_t cluster_levels(Instance &I, SLevels<M> &P, int lA) {
-        P.n = I.lc0 - lA;
-        if (lA < 1 || P.n < 1 || P.n > kMaxSL) return (size_t)-1;
-        P.nu = I.mg_nu_c;
-        P.nu_top = I.mg_nu_c;
-        size_t off = 0, nmax = 0;
-        auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 15) & ~(size_t)15; return (int)o; };
-        for (int q = 0; q < P.n; ++q) {
-            Level &L = I.lev[lA + q];
-            SLevel<M> &S = P.L[q];
-            if (L.g.nx % kClusterCtas != 0) return (size_t)-1;
-            const int sx = L.g.nx / kClusterCtas;
-            if (sx % L.r[0] != 0) return (size_t)-1;
-            S.g = to_dev(L.g);
-            S.sx = sx;
-            for (int a = 0; a < 3; ++a) { S.c[a] = (const M *)L.c[a]; S.r[a] = L.r[a]; }
-            S.idiag = (const M *)L.idiag;
-            S.rsx = 1.0f / (float)sx;
-            S.rsx1 = 1.0f / (float)(sx + 1);
-            S.rny = 1.0f / (float)L.g.ny;
-            S.rny1 = 1.0f / (float)(L.g.ny + 1);
-            S.rhx = 1.0f / (float)((sx + 1) / 2);
-            const size_t n = (size_t)sx * L.g.ny * L.g.nz;
-            nmax = n > nmax ? n : nmax;
-            S.ox = take(n * sizeof(M));
-            S.ob = take(n * sizeof(M));
-            S.oi = take(n * sizeof(M));
-            S.oc[0] = take((size_t)(sx + 1) * L.g.ny * L.g.nz * sizeof(M));
-            S.oc[1] = take((size_t)sx * (L.g.ny + 1) * L.g.nz * sizeof(M));
-            S.oc[2] = take(L.g.dim == 3 ? (size_t)sx * L.g.ny * (L.g.nz + 1) * sizeof(M) : 0);
-        }
-        P.ors = take(nmax * sizeof(M));
-        size_t tot = cta_levels(I, P.C, I.lc0, off, false);
-        return P.C.n > kMaxCL ? (size_t)-1 : tot;
-    }
-
     // x / b of level l (level 0 works in place on the Krylov vectors z / r)
     static M *lx(Instance &I, int l, V *z) { return l == 0 ? (M *)z : (M *)I.lev[l].x; }
     static M *lb(Instance &I, int l, V *r) { return l == 0 ? (M *)r : (M *)I.lev[l].b; }
@@ -376,14 +317,12 @@ template <typename T> struct Impl {
         Level &L = I.lev[l];
         GridD g = to_dev(L.g);
         L3 LL = launch3((L.g.nx + 1) / 2, L.g.ny, L.g.nz);
-        int ps = l == 0 && !with_dot ? prof_begin(I, OSCAR_KID_RBGS0) : -1;
         if (with_dot)
             launchk(k_mg_rbgs_dot<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour,
                     I.partials, I.ticket, I.scal), ++I.nlaunch;
         else
             launchk(k_mg_rbgs<DIM, M, false>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b,
                     colour, g, 0, 0, 0, (const M *)nullptr), ++I.nlaunch;
-        prof_end(I, ps);
     }
     // the first post-smoothing half sweep (colour 1) of level l with the
     // prolongation from level l + 1 (x of level l + 1 in xc) folded in
@@ -428,7 +367,7 @@ template <typename T> struct Impl {
     // k_cg_update for the finest level, the restriction for the others).
     template <int DIM>
     static int vcycle_d(Instance &I, V *r, V *z) {
-        const int lk = I.lA > 0 ? I.lA : I.lc0;   // first level not worked by per-level kernels
+        const int lk = I.lc0;   // first level not worked by per-level kernels
         for (int l = 0; l < lk; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -437,19 +376,9 @@ template <typename T> struct Impl {
                 if (s > 0) smooth_level<DIM>(I, l, 0, x, b);
                 smooth_level<DIM>(I, l, 1, x, b);
             }
-            int ps = l == 0 ? prof_begin(I, OSCAR_KID_RESID0) : -1;
             resid_restrict<DIM>(I, L, C, x, b, lb(I, l + 1, r), lx(I, l + 1, z), l + 1 < lk ? 1 : 0);
-            prof_end(I, ps);
         }
-        if (I.lA > 0) {
-            if constexpr (sizeof(M) == sizeof(float)) {
-                SLevels<M> P;
-                cluster_levels(I, P, I.lA);
-                P.b_top = lb(I, I.lA, r);
-                P.x_top = lx(I, I.lA, z);
-                launch_cluster(k_mg_cluster<DIM, M>, I.cl_smem, I.stream, P), ++I.nlaunch;
-            }
-        } else {
+        {
             CLevels<M> P;
             cta_levels(I, P, I.lc0);
             P.b_top = lb(I, I.lc0, r);
@@ -493,7 +422,6 @@ template <typename T> struct Impl {
         OSCAR_TRY(vcycle_d<DIM>(I, r, z));
         if (I.lc0 == 0)   // the whole V-cycle ran in the coarse CTA: r.z on its own
             launchk(k_cg_dot_rz<V>, kRedBlocks, BS, 0, I.stream, n, r, z, I.partials, I.ticket, I.scal), ++I.nlaunch;
-        int ps = prof_begin(I, OSCAR_KID_CG_APPLY);
         if constexpr (sizeof(V) == sizeof(float)) {
             L3 LA = launch_rpt(I.g, kApplyRows);
             launchk(k_cg_pz_apply<DIM, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info, c3(I.lev[0].c),
@@ -503,7 +431,6 @@ template <typename T> struct Impl {
             launchk(k_cg_apply_dot<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.lev[0].c), p, Ap,
                     I.partials, I.ticket, L.nblocks, I.scal), ++I.nlaunch;
         }
-        prof_end(I, ps);
         L3 LU = launch_rpt(I.g, kUpdateRows);
         launchk(k_cg_update<V, kUpdateRows>, LU.grid, LU.block, 0, I.stream, g, x, r, p, Ap, (const V *)I.lev[0].idiag,
                 z, I.partials, I.ticket, I.scal, I.ctl, I.P.cg_maxit, target_slot, xfresh, h), ++I.nlaunch;
@@ -578,11 +505,9 @@ template <typename T> struct Impl {
         C3<T> Gc0 = c3(&I.G[0]), Gc1 = c3(&I.G[3]), Gc2 = c3(&I.G[6]);
         for (int corr = 0; corr < I.P.n_piso; ++corr) {
             launchk(k_vel_grad<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(v), (T)vin0, Gp0, Gp1, Gp2), ++I.nlaunch;
-            int ps = prof_begin(I, OSCAR_KID_MOMENTUM);
             launchk(k_momentum_H<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(v), c3(I.vold), c3(I.phic), al,
                                                                    tp(I.rA), fl, (T)vin0, (T)dt, Gc0, Gc1, Gc2,
                                                                    p3(I.hbya)), ++I.nlaunch;
-            prof_end(I, ps);
             launchk(k_phistar<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.hbya[0]), tp(I.rA), tp(I.fst[0]),
                                                                     (T)vin0, tp(I.phis[0])), ++I.nlaunch;
             launchk(k_phistar<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.hbya[1]), tp(I.rA), tp(I.fst[1]),
@@ -757,14 +682,18 @@ template <typename T> struct Impl {
     // Launch step `kind` (graph, or eager loops) and read its control words back.
     // launch one step (graph, or the eager sequence) and the copies of its
     // device scalars back to the host, without waiting
+    static bool eager_now(const Instance &I) { return I.eager || (I.prof && I.prof->enabled); }
     static int run_launch(Instance &I, int kind, double dt, int N) {
-        if (!I.eager) OSCAR_TRY(build(I, kind, dt));
+        const bool eager = eager_now(I);
+        if (!eager) OSCAR_TRY(build(I, kind, dt));
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
         for (int q = 0; q < C_COUNT; ++q) I.ctl_host[q] = 0;
         I.ctl_host[C_N] = N;
-        if (I.eager) {
+        if (eager) {
             long long l0 = I.nlaunch, d0 = 0, d1 = 0;
+            t_prof = (I.prof && I.prof->enabled) ? I.prof : nullptr;
             int rc = kind == 0 ? body_drag(I, dt) : kind == 1 ? body_relax(I, dt, &d0, &d1) : body_standard(I, dt);
+            t_prof = nullptr;
             if (rc) return rc;
             I.nexec += I.nlaunch - l0;
         } else if (cudaGraphLaunch(I.gslot[kind].exec, I.stream) != cudaSuccess) {
@@ -793,7 +722,7 @@ template <typename T> struct Impl {
         const GraphSlot &G = I.gslot[kind];
         int its = I.ctl_host[C_ITSUM];
         int trips = kind == 1 ? I.ctl_host[C_K] : 1;
-        if (!I.eager) {
+        if (!eager_now(I)) {
             long long outer_trips = sizeof(T) == sizeof(double) ? 0 : (long long)I.ctl_host[C_OSUM];
             I.nexec += G.n_pre + (long long)(kind == 1 ? trips : 0) * G.n_body + (long long)its * I.n_cg_body +
                        outer_trips * I.n_outer_body;
@@ -856,49 +785,6 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                          : cudaFuncSetAttribute(k_mg_coarse_pack<2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 (int)budget);
     if (e != cudaSuccess) return OSCAR_E_CUDA;
-    // mixed path, opt-in (OSCAR_CLUSTER=1): the levels between the per-level
-    // kernels and the coarse CTA go to the cluster kernel when they split
-    // into aligned slabs and fit. On the 3D constriction it measured slower
-    // than the per-level launches (cluster barriers plus distributed-shared-
-    // memory halo reads cost about as much per phase as a dependent launch,
-    // and the per-launch reload of the slabs is not amortised).
-    I.lA = -1;
-    I.cl_smem = 0;
-    if constexpr (sizeof(T) == sizeof(float)) {
-        const char *ec = getenv("OSCAR_CLUSTER");
-        const bool want = ec && atoi(ec) == 1;
-        SLevels<T> S;
-        for (int lA = 1; want && lA < I.lc0; ++lA) {
-            size_t sm = Impl<T>::cluster_levels(I, S, lA);
-            if (sm == (size_t)-1 || sm > budget) continue;
-            void (*kern)(SLevels<T>) = I.g.dim == 3 ? k_mg_cluster<3, T> : k_mg_cluster<2, T>;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget) != cudaSuccess) {
-                cudaGetLastError();
-                break;
-            }
-            cudaLaunchConfig_t cfg;
-            memset(&cfg, 0, sizeof(cfg));
-            cfg.gridDim = dim3(kClusterCtas);
-            cfg.blockDim = dim3(kCtaThreads);
-            cfg.dynamicSmemBytes = sm;
-            cudaLaunchAttribute at[1];
-            at[0].id = cudaLaunchAttributeClusterDimension;
-            at[0].val.clusterDim.x = kClusterCtas;
-            at[0].val.clusterDim.y = 1;
-            at[0].val.clusterDim.z = 1;
-            cfg.attrs = at;
-            cfg.numAttrs = 1;
-            int ncl = 0;
-            if (cudaOccupancyMaxActiveClusters(&ncl, (void *)kern, &cfg) != cudaSuccess || ncl < 1) {
-                cudaGetLastError();
-                break;
-            }
-            I.lA = lA;
-            I.cl_smem = sm;
-            break;
-        }
-    }
     int rc = Impl<T>::interface_(I, I.alpha);
     I.nexec += I.nlaunch - l0;
     return rc;
@@ -947,80 +833,6 @@ template <typename T> int Solver<T>::standard_step(Instance &I, double dt) {
     if (rc == OSCAR_E_CUDA || rc == OSCAR_E_TIMEOUT) return rc;
     I.last_E = I.scal_host[S_E];
     I.last_N = 1;
-    return rc;
-}
-
-// eager launches of one kernel class on the current state, timed with events
-template <typename T> int Solver<T>::profile_kernel(Instance &I, int kid, int reps, double *avg_ms) {
-    using X = Impl<T>;
-    using V = T;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return OSCAR_E_CUDA;
-    GridD g = to_dev(I.g);
-    L3 L = launch3(I.g), LR = launch_rows(I.g, kRedBlocks), LA = launch_rpt(I.g, kApplyRows);
-    double dt = I.last_dt > 0 ? I.last_dt : 1e-7;
-    Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
-    Level &L0 = I.lev[0];
-    V *r = (V *)I.cg_r, *z = (V *)I.cg_z;
-    cudaEventRecord(e0, I.stream);
-    for (int rep = 0; rep < reps; ++rep) {
-        if (kid == OSCAR_KID_RBGS0) {
-            if (I.g.dim == 3) X::template smooth_level<3>(I, 0, rep & 1, (T *)z, (const T *)r);
-            else X::template smooth_level<2>(I, 0, rep & 1, (T *)z, (const T *)r);
-        } else if (kid == OSCAR_KID_RESID0) {
-            if (I.nlev > 1) {
-                Level &C = I.lev[1];
-                if (I.g.dim == 3) X::template resid_restrict<3>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
-                else X::template resid_restrict<2>(I, L0, C, (const T *)z, (const T *)r, (T *)C.b, (T *)C.x, 0);
-            }
-        } else if (kid == OSCAR_KID_CG_APPLY) {   // the operator apply of the PCG iteration
-            if constexpr (sizeof(V) == sizeof(float)) {
-                if (I.g.dim == 3)
-                    launchk(k_cg_pz_apply<3, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info,
-                            X::c3(I.lev[0].c), (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket,
-                            LA.nblocks, I.scal),
-                        ++I.nlaunch;
-                else
-                    launchk(k_cg_pz_apply<2, T, V, kApplyRows>, LA.grid, LA.block, 0, I.stream, g, I.info,
-                            X::c3(I.lev[0].c), (const V *)I.cg_z, (V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket,
-                            LA.nblocks, I.scal),
-                        ++I.nlaunch;
-            } else {
-                if (I.g.dim == 3)
-                    launchk(k_cg_apply_dot<3, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
-                            (const V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal), ++I.nlaunch;
-                else
-                    launchk(k_cg_apply_dot<2, T, V>, LR.grid, LR.block, 0, I.stream, g, I.info, X::c3(I.lev[0].c),
-                            (const V *)I.cg_p, (V *)I.cg_Ap, I.partials, I.ticket, LR.nblocks, I.scal), ++I.nlaunch;
-            }
-        } else if (kid == OSCAR_KID_MOMENTUM) {
-            C3<T> Gc0 = X::c3(&I.G[0]), Gc1 = X::c3(&I.G[3]), Gc2 = X::c3(&I.G[6]);
-            if (I.g.dim == 3)
-                launchk(k_momentum_H<3, T>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.u_cr), X::c3(I.vold),
-                                                                     X::c3(I.phic), (const T *)I.alpha_new,
-                                                                     (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
-                                                                     X::p3(I.hbya)), ++I.nlaunch;
-            else
-                launchk(k_momentum_H<2, T>, L.grid, L.block, 0, I.stream, g, I.info, X::c3(I.u_cr), X::c3(I.vold),
-                                                                     X::c3(I.phic), (const T *)I.alpha_new,
-                                                                     (const T *)I.rA, fl, T(0), (T)dt, Gc0, Gc1, Gc2,
-                                                                     X::p3(I.hbya)), ++I.nlaunch;
-        } else if (kid == OSCAR_KID_TRANSPORT) {
-            X::transport(I, I.phi_cr, dt);
-        } else {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return OSCAR_E_INVALID_ARG;
-        }
-    }
-    cudaEventRecord(e1, I.stream);
-    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
-    float ms = 0.f;
-    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = OSCAR_E_CUDA;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (cudaGetLastError() != cudaSuccess) rc = OSCAR_E_CUDA;
-    *avg_ms = reps > 0 ? ms / reps : 0.0;
     return rc;
 }
 

@@ -134,6 +134,35 @@ def channel_bubble_2d(nx: int = 128, ny: int = 16, Lx: float = 800e-6, Ly: float
 
 
 # ----------------------------------------------------------------------------
+# Benchmark case 1 of Section 5.1: air bubble in ethanol, 600x100 um channel
+# ----------------------------------------------------------------------------
+def bubble_film_2d(Ca: float = 1e-2, h: float = 1e-6, Lx: float = 600e-6, W: float = 100e-6,
+                   bubble_len: float = 200e-6, bubble_x0: float = 20e-6, c_cfl: float = 0.01,
+                   mu_liquid: float = 1.2e-3, rho_liquid: float = 789.0, **overrides) -> Case:
+    """The paper's first benchmark (Section 5.1): a non-wetting air bubble
+    (rho 1, mu 18 uPa s) in ethanol (rho 789, mu 1.2 mPa s), sigma 20 mN/m, in
+    a straight 2D channel 600 um long and 100 um wide; the bubble starts as a
+    full-width rectangle 200 um long whose left end is 20 um from the inlet.
+    The liquid wets the walls (0 degrees through the liquid, i.e. 180 degrees
+    through the air, alpha = 1), and ethanol is injected at U = Ca sigma / mu.
+    The drag steps use dt_vd = 0.01 dt_CFL as in the paper. Uniform square
+    cells of size h (1 um gives 600x100 cells)."""
+    sigma = 0.02
+    nx, ny = int(round(Lx / h)), int(round(W / h))
+    U = Ca * sigma / mu_liquid
+    x = _cell_centres(nx, h)
+    frac = np.clip((np.minimum(x + h / 2, bubble_x0 + bubble_len) - np.maximum(x - h / 2, bubble_x0)) / h, 0.0, 1.0)
+    alpha0 = np.broadcast_to(frac[None, :], (ny, nx)).copy()
+    solid = np.zeros((ny, nx), np.uint8)
+    p = default_params(dim=2, nx=nx, ny=ny, nz=1, hx=h, hy=h, hz=h,
+                       rho1=1.0, rho2=rho_liquid, mu1=1.8e-5, mu2=mu_liquid, sigma=sigma,
+                       theta_deg=180.0, U_inlet=U, alpha_inlet=0.0)
+    p.update(overrides)
+    return Case("bubble_film_2d", p, solid, alpha0,
+                dict(c_cfl=c_cfl, Ca=Ca, W=W, bubble_len=bubble_len, t_end=bubble_len / U))
+
+
+# ----------------------------------------------------------------------------
 # 3D constricted square channel, CO2 slug (256x64x64 over 1600x100x100 um)
 # ----------------------------------------------------------------------------
 def constricted_channel_3d(nx: int = 256, ny: int = 64, nz: int = 64,

@@ -48,7 +48,7 @@ class oscar_stats_t(C.Structure):
         ("cg_iters_total", C.c_longlong), ("cg_iters_last", C.c_int), ("mg_levels", C.c_int),
         ("phase_volume", C.c_double), ("n_fluid", C.c_longlong), ("cell_updates", C.c_longlong),
         ("device_bytes", C.c_size_t), ("kernel_launches", C.c_longlong),
-        ("mg_first_cta_level", C.c_int), ("mg_first_cluster_level", C.c_int),
+        ("mg_first_cta_level", C.c_int),
     ]
 
 
@@ -56,9 +56,8 @@ EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", 
            "oscar_drag_step_async", "oscar_relax_async", "oscar_standard_step_async", "oscar_wait",
            "oscar_footprint", "oscar_query",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
-           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_kernel",
+           "oscar_strerror", "oscar_profile", "oscar_profile_read",
            "oscar_phase_volume_noalloc"]
-KID_RBGS0, KID_CG_APPLY, KID_MOMENTUM, KID_TRANSPORT, KID_RESID0 = range(5)
 
 _lib = None
 
@@ -73,7 +72,7 @@ def load(path: str = LIB_PATH):
     lib = C.CDLL(path)
     dp = C.POINTER(C.c_double)
     H = C.c_void_p
-    lib.oscar_timesteps.argtypes = [C.POINTER(oscar_params), C.c_double, dp]
+    lib.oscar_timesteps.argtypes = [C.POINTER(oscar_params), C.POINTER(C.c_uint8), C.c_double, dp]
     lib.oscar_create.argtypes = [C.POINTER(oscar_params), C.POINTER(C.c_uint8), dp, C.c_void_p, C.POINTER(H)]
     lib.oscar_drag_step.argtypes = [H, C.c_double]
     lib.oscar_relax.argtypes = [H, C.c_double, C.c_int, C.POINTER(C.c_int), dp]
@@ -92,8 +91,8 @@ def load(path: str = LIB_PATH):
     lib.oscar_strerror.argtypes = [C.c_int]
     lib.oscar_strerror.restype = C.c_char_p
     lib.oscar_profile.argtypes = [H, C.c_int]
-    lib.oscar_profile_read.argtypes = [H, C.c_int, dp, C.POINTER(C.c_longlong), C.c_int]
-    lib.oscar_profile_kernel.argtypes = [H, C.c_int, C.c_int, dp]
+    lib.oscar_profile_read.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.c_char_p, C.c_size_t,
+                                       C.POINTER(C.c_uint), dp, C.POINTER(C.c_longlong)]
     lib.oscar_phase_volume_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_double, C.c_void_p,
                                                C.c_void_p]
     _lib = lib
@@ -122,11 +121,19 @@ def oscar_footprint(params: dict) -> int:
     return int(out.value)
 
 
-def oscar_timesteps(params: dict, c_cfl: float):
+def oscar_timesteps(params: dict, c_cfl: float, solid=None):
+    """(dt_CFL, dt_B, dt_vd, N); with a solid mask the CFL velocity is the mean
+    speed through the narrowest x cross-section."""
     lib = load()
     out = (C.c_double * 4)()
     P = make_params(params)
-    _check(lib.oscar_timesteps(C.byref(P), c_cfl, out), "oscar_timesteps")
+    sp = None
+    if solid is not None:
+        s = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        if s.size != params["nx"] * params["ny"] * (params["nz"] if params["dim"] == 3 else 1):
+            raise ValueError("solid mask does not match the grid")
+        sp = s.ctypes.data_as(C.POINTER(C.c_uint8))
+    _check(lib.oscar_timesteps(C.byref(P), sp, c_cfl, out), "oscar_timesteps")
     return out[0], out[1], out[2], int(out[3])
 
 
@@ -227,20 +234,24 @@ class Oscar:
         _check(self.lib.oscar_set_field(self.h, which, a.ctypes.data_as(C.POINTER(C.c_double)), n), "oscar_set_field")
 
     def profile(self, enable: bool):
+        """Start (clearing the last recording) or stop in-step kernel timing:
+        while on, steps run eagerly with CUDA events around every launch."""
         _check(self.lib.oscar_profile(self.h, 1 if enable else 0), "oscar_profile")
 
-    def profile_read(self, kid: int, reset: bool = False):
-        ms = C.c_double(0.0)
-        n = C.c_longlong(0)
-        _check(self.lib.oscar_profile_read(self.h, kid, C.byref(ms), C.byref(n), 1 if reset else 0),
-               "oscar_profile_read")
-        return ms.value, n.value
-
-    def profile_kernel(self, kid: int, reps: int = 100) -> float:
-        """Mean device time [ms] of one launch of kernel class kid (CUDA events)."""
-        ms = C.c_double(0.0)
-        _check(self.lib.oscar_profile_kernel(self.h, kid, reps, C.byref(ms)), "oscar_profile_kernel")
-        return ms.value
+    def profile_read(self) -> list:
+        """[(kernel name, grid blocks, total ms, launches)] of the recording."""
+        cnt = C.c_int(0)
+        self.lib.oscar_profile_read(self.h, 0, C.byref(cnt), None, 0, None, None, None)
+        out = []
+        buf = C.create_string_buffer(512)
+        for i in range(cnt.value):
+            g = C.c_uint(0)
+            ms = C.c_double(0.0)
+            n = C.c_longlong(0)
+            _check(self.lib.oscar_profile_read(self.h, i, None, buf, 512, C.byref(g), C.byref(ms), C.byref(n)),
+                   "oscar_profile_read")
+            out.append((buf.value.decode(errors="replace"), g.value, ms.value, n.value))
+        return out
 
     def stats(self) -> dict:
         st = oscar_stats_t()

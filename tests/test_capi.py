@@ -50,11 +50,23 @@ def test_timesteps_match_oracle(lib, case):
          "constriction": lambda: inputs.constricted_channel_3d(nx=16, ny=8, nz=8),
          "micromodel": lambda: inputs.micromodel_2d(nx=64, ny=32)}[case]()
     cc = c.meta["c_cfl"]
-    a = oscar.oscar_timesteps(c.params, cc)
-    b = oracle.timesteps(c.params, cc)
-    for x, y in zip(a[:3], b[:3]):
-        assert x == pytest.approx(y, rel=1e-15)
-    assert a[3] == b[3]
+    for solid in (None, c.solid):
+        a = oscar.oscar_timesteps(c.params, cc, solid)
+        b = oracle.timesteps(c.params, cc, solid)
+        for x, y in zip(a[:3], b[:3]):
+            assert x == pytest.approx(y, rel=1e-15)
+        assert a[3] == b[3]
+
+
+def test_timesteps_reject_a_blocked_channel(lib):
+    """A column with no fluid while the inlet has some: no path to the outlet."""
+    c = inputs.channel_bubble_2d(nx=16, ny=4)
+    s = c.solid.copy()
+    s[:, 7] = 1
+    with pytest.raises(oscar.OscarError):
+        oscar.oscar_timesteps(c.params, 0.1, s)
+    with pytest.raises(ValueError):
+        oracle.timesteps(c.params, 0.1, s)
 
 
 def test_create_rejects_bad_arguments(lib):

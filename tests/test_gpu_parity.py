@@ -133,34 +133,61 @@ def test_fp64_early_exit_residual_matches_oracle():
     compare(g, o, 2, 1e-10)
 
 
+def _spread_bounds(which):
+    """Per-field parity bounds of the full bubble run: 1e-10 relative, or four
+    times the oracle's own spread under one-ulp perturbations of alpha0 where
+    that spread is larger (tests/golden/bubble_rounding_spread.json, written by
+    tests/golden/make_bubble_rounding_spread.py from oracle runs only)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bubble_rounding_spread.json")
+    spread = json.load(open(path))[which]
+    return {k: max(1e-10, 4.0 * v) for k, v in spread.items()}
+
+
+def _compare_bounded(g, o, bounds, skip=()):
+    worst = {}
+    for name, wg, wo in fields_for(2):
+        if name in skip:
+            continue
+        x, y = g.field(wg), o.field(wo)
+        if name == "kappa":
+            a_or = o.field(oracle.ALPHA)
+            band = (a_or > BAND[0]) & (a_or < BAND[1])
+            x, y = x[band], y[band]
+        worst[name] = (rel_err(x, y), bounds.get(name, 1e-10))
+    bad = {k: v for k, v in worst.items() if not v[0] <= v[1]}
+    assert not bad, f"fields over their bound (error, bound): {bad}"
+    return worst
+
+
 def test_fp64_bubble_channel_full_run_matches_oracle():
     """The 128x16 bubble channel: 20 drag steps, each followed by up to 50
     relaxation sub-steps (tolerance 1e-6 on max |du_cr|/U), and 2000 standard
-    steps at the relaxation time-step. alpha, p and kappa stay within 1e-10
-    relative. The velocity and flux fields carry the rounding noise of 1000
-    pressure solves (condition number ~1e7 at the 1000:1.2 density ratio),
-    amplified by the parasitic-current dynamics: the oracle itself moves by
-    6e-10 on these fields when only its CG tolerance changes from 1e-14 to
-    1e-15, and the differences grow with the number of solves (3000 here,
-    6000 in the standard run), so they are held to 1e-8."""
+    steps at the relaxation time-step, against the oracle with exact (banded
+    Cholesky) pressure solves. alpha, p, p_vd, p_cr and kappa stay within
+    1e-10 relative. The velocity and flux fields are held to four times the
+    spread of the oracle's own runs when alpha0 is perturbed by one ulp (at
+    most 7e-10 after the OSCAR run, 3.3e-9 after the standard run): at the
+    1000:1.2 density ratio the parasitic-current dynamics amplify rounding
+    differences over thousands of pressure solves, so no differently rounded
+    implementation can agree more closely; where that spread is below 2.5e-11
+    the bound stays 1e-10."""
     c = inputs.channel_bubble_2d(cg_rtol=1e-15, cg_maxit=400)   # oracle: exact banded solves
-    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"])
+    dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, c.meta["c_cfl"], c.solid)
     assert N == 50
     g, o, kg, ko = run_oscar_pair(c, c.meta["n_drag"], N, dt_vd, dt_vd / N)
     assert kg == ko
-    vel = ("ux", "uy", "uvdx", "uvdy", "ucrx", "ucry", "phi_vd_x", "phi_vd_y", "phi_cr_x", "phi_cr_y")
-    worst = compare(g, o, 2, 1e-10, skip=vel)
-    worst.update(compare(g, o, 2, 1e-8, skip=tuple(n for n, _, _ in fields_for(2) if n not in vel)))
-    print("oscar worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
+    worst = _compare_bounded(g, o, _spread_bounds("oscar"))
+    print("oscar (error, bound)", {k: f"{v[0]:.1e}/{v[1]:.1e}" for k, v in worst.items()})
     gs = ox.Oscar(c.params, c.solid, c.alpha0)
     os_ = oracle.OracleState(c.params, c.solid, c.alpha0)
     for _ in range(c.meta["n_standard"]):
         gs.standard_step(dt_vd / N)
         os_.standard_step(dt_vd / N)
     crf = ("ucrx", "ucry", "phi_cr_x", "phi_cr_y")
-    worst = compare(gs, os_, 2, 1e-10, skip=crf + vel)
-    worst.update(compare(gs, os_, 2, 1e-8, skip=crf + tuple(n for n, _, _ in fields_for(2) if n not in vel)))
-    print("standard worst rel err", {k: f"{v:.1e}" for k, v in worst.items()})
+    worst = _compare_bounded(gs, os_, _spread_bounds("standard"), skip=crf)
+    print("standard (error, bound)", {k: f"{v[0]:.1e}/{v[1]:.1e}" for k, v in worst.items()})
 
 
 def _bubble_velocity(st, is_oracle):
@@ -182,40 +209,9 @@ def test_mixed_precision_within_tolerance(make):
     assert vg == pytest.approx(vo, rel=5e-3)
 
 
-def test_mixed_cluster_multigrid_matches_per_level_kernels(monkeypatch):
-    """The thread-block-cluster kernel for the middle multigrid levels
-    (128x32x32: levels 64x16x16 and 32x8x8 as x-slabs of 16 CTAs, the levels
-    from 16x4x4 down on rank 0) applies the same V-cycle as the per-level
-    kernels; both runs solve to the same tolerance and agree within the mixed
-    path's tolerance, with the cluster kernel actually in use in the first."""
-    c = inputs.random_small_case(8, 128, 32, nz=32, dim=3)
-    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0, cg_rtol=1e-8)
-    p = dict(c.params, precision=inputs.PREC_MIXED)
-    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, 0.02)
-    out = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("OSCAR_CLUSTER", flag)
-        g = ox.Oscar(p, c.solid, c.alpha0)
-        st = g.stats()
-        g.drag_step(dt_vd, strict=False)
-        _, kf, _ = g.relax(dt_vd / N, 3, strict=False)
-        out[flag] = dict(st=st, kf=kf, alpha=g.field(ox.FIELD_ALPHA), p=g.field(ox.FIELD_P_CR),
-                         u=g.field(ox.FIELD_U_CR), pvd=g.field(ox.FIELD_P_VD))
-        g.close()
-    assert out["1"]["st"]["mg_first_cluster_level"] == 1
-    assert out["0"]["st"]["mg_first_cluster_level"] == -1
-    assert out["1"]["st"]["mg_first_cta_level"] == out["0"]["st"]["mg_first_cta_level"] == 3
-    a, b = out["1"], out["0"]
-    assert np.all(np.isfinite(a["alpha"])) and np.all(np.isfinite(a["u"]))
-    assert np.abs(a["alpha"] - b["alpha"]).max() <= 1e-5
-    for key in ("p", "pvd", "u"):
-        scale = np.abs(b[key]).max()
-        assert np.abs(a[key] - b[key]).max() <= 5e-3 * scale, key
-
-
 def _batch_setup(case, n_sub):
     p = dict(case.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
-    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, case.meta["c_cfl"])
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, case.meta["c_cfl"], case.solid)
     dt_cr = 0.99 * dt_b
     return p, n_sub * dt_cr, dt_cr
 
@@ -335,7 +331,7 @@ def test_full_size_invariants(which):
     c = (inputs.constricted_channel_3d(cg_rtol=1e-8) if which == "constriction_3d"
          else inputs.micromodel_2d(cg_rtol=1e-8))
     p = c.params
-    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"])
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
     g = ox.Oscar(p, c.solid, c.alpha0)
     v0 = g.stats()["phase_volume"]
     g.drag_step(dt_vd)
@@ -356,3 +352,35 @@ def test_full_size_invariants(which):
     phix = g.field(ox.FIELD_PHI_VD)
     v1 = g.stats()["phase_volume"]
     assert abs(v1 - v0) <= 2.0 * abs(phix[..., 0]).sum() * dt_vd + 1e-6 * v0
+
+
+def test_bench_workload_long_run_stays_bounded():
+    """The bench workload (3D constriction 256x64x64, mixed precision, the
+    time steps of the bench) for 50 OSCAR steps, more than the bench runs
+    (warm-up, timed and end-to-end steps): every drag step and relaxation
+    returns 0 (solves converged, nothing non-finite), alpha stays in [0, 1],
+    the drag Courant number stays below 1 and the phase volume grows by what
+    the inlet injects (nothing of the injected phase reaches the outlet)."""
+    c = inputs.constricted_channel_3d(cg_rtol=1e-8)
+    p = c.params
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+    g = ox.Oscar(p, c.solid, c.alpha0)
+    v0 = g.stats()["phase_volume"]
+    S = [p["hy"] * p["hz"], p["hx"] * p["hz"], p["hx"] * p["hy"]]
+    h = [p["hx"], p["hy"], p["hz"]]
+    inflow = 0.0
+    for step in range(50):
+        # the drag step transports alpha with the drag flux of the previous step (Eq. VOFd)
+        inflow += g.field(ox.FIELD_PHI_VD)[..., 0].sum() * dt_vd
+        assert g.drag_step(dt_vd) == 0
+        rc, kf, _ = g.relax(dt_vd / N, N)
+        assert rc == 0 and 1 <= kf <= N
+        if step % 10 == 9:
+            a = g.field(ox.FIELD_ALPHA)
+            assert np.isfinite(a).all()
+            assert a.min() >= -1e-5 and a.max() <= 1 + 1e-5
+            co = max(np.abs(g.field(ox.FIELD_PHI_VD + d)).max() / S[d] * dt_vd / h[d] for d in range(3))
+            assert co < 1.0, co
+    v1 = g.stats()["phase_volume"]
+    assert v1 - v0 == pytest.approx(p["alpha_inlet"] * inflow, rel=2e-3)
+    g.close()

@@ -45,6 +45,36 @@ def test_timesteps_uses_smallest_spacing():
     assert N == math.floor(dt_vd / dt_b) + 1
 
 
+def test_timesteps_cfl_velocity_is_the_narrowest_section_mean():
+    """Section 2.2, dt_CFL = dx / u: with a solid mask u is the mean speed of
+    the injected flux through the narrowest x cross-section. Counted by brute
+    force from the mask: a 2D channel with a 3-of-4-cell block in one column
+    carries 4 U there; a straight channel carries U."""
+    c = inputs.channel_bubble_2d(nx=16, ny=4)
+    s = c.solid.copy()
+    s[1:, 9] = 1
+    open_ = oracle.timesteps(c.params, 0.3, c.solid)
+    blocked = oracle.timesteps(c.params, 0.3, s)
+    none = oracle.timesteps(c.params, 0.3)
+    U = c.params["U_inlet"]
+    assert open_[0] == none[0] == pytest.approx(c.params["hx"] / U, rel=1e-15)
+    assert blocked[0] == pytest.approx(c.params["hx"] / (4.0 * U), rel=1e-15)
+    assert blocked[2] == pytest.approx(0.3 * blocked[0], rel=1e-15)
+    assert blocked[1] == none[1]                      # Brackbill does not depend on the flow
+
+
+def test_timesteps_constriction_throat():
+    """3D constriction to 30 % of the width (256x64x64): the voxelised throat
+    is 20x20 cells (|y - W/2| <= 15 um at 1.5625 um cells: the 10 cell centres
+    on each side within 15 um), the inlet 64x64, so u = 4096/400 U = 10.24 U."""
+    c = inputs.constricted_channel_3d()
+    y = (np.arange(64) + 0.5) * 1.5625e-6 - 50e-6
+    n_throat = int((np.abs(y) <= 15e-6).sum())
+    assert n_throat == 20
+    dt_cfl = oracle.timesteps(c.params, 0.1, c.solid)[0]
+    assert dt_cfl == pytest.approx(c.params["hx"] / (c.params["U_inlet"] * 64 * 64 / n_throat ** 2), rel=1e-14)
+
+
 # ---------------------------------------------------------------------------
 # Pressure operator and solver
 # ---------------------------------------------------------------------------
