@@ -349,6 +349,167 @@ def time_to_solution():
     return res
 
 
+def splitting_study(cas=(1e-3, 1e-4, 1e-5, 1e-6), n_drag=10, piso_full_max=12000, piso_sample=1500,
+                    budget_s=25.0):
+    """OSCAR against standard (PISO) time-stepping across capillary numbers on
+    the 128x16 bubble channel (Sections 5.1-5.3: the speed-up grows as Ca
+    falls because the relaxation exits early, k_f << N). Mixed precision,
+    pressure solves to 1e-8, the paper's exit test E_k < 1e-4 (Section 3.2),
+    dt_vd = 0.29 dt_CFL, dt_cr = dt_vd / N; standard stepping at dt_cr. Per Ca:
+    k_f statistics, OSCAR wall seconds for n_drag global steps, the standard
+    run over the same physical time (n_drag N steps) when that is at most
+    piso_full_max steps, else its time extrapolated from piso_sample steps (the
+    paper extrapolates its slowest PISO runs the same way), and the splitting
+    error of Eq. L2split: the largest over the global steps t_n = n dt_vd and
+    over beta in (|u|, p, alpha) of ||beta_OSCAR - beta_PISO||_2 / ||beta_PISO||_2,
+    with u and p of OSCAR its reconstructed fields (Section 3.2). A Ca whose
+    OSCAR steps pass budget_s seconds stops early; its standard-stepping time
+    then covers the drag steps done."""
+    from paper_2105_10576_gb300 import oscar as ox
+    out = {"workload": f"2D bubble channel 128x16 over 800x100 um (config 0 geometry and fluids), {n_drag} drag "
+                       "steps at 0.29 dt_CFL, E_k < 1e-4 exit, mixed precision, solves to 1e-8",
+           "cases": []}
+    for Ca in cas:
+        c = inputs.channel_bubble_2d(Ca=Ca)
+        p = dict(c.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8, conv_mode=inputs.CONV_PRES_RESID,
+                 conv_tol=1e-4)
+        dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+        go = ox.Oscar(p, c.solid, c.alpha0)
+        n_piso = n_drag * N
+        full = n_piso <= piso_full_max
+        gp = ox.Oscar(p, c.solid, c.alpha0) if full else None
+        # one untimed step each: graph construction
+        go.drag_step(dt_vd)
+        go.relax(dt_vd / N, N)
+        go.close()
+        go = ox.Oscar(p, c.solid, c.alpha0)
+        kfs, t_oscar, t_piso, err = [], 0.0, 0.0, {"alpha": 0.0, "p": 0.0, "u": 0.0}
+        for n in range(n_drag):
+            if t_oscar > budget_s:
+                break
+            t0 = time.perf_counter()
+            go.drag_step(dt_vd)
+            _, kf, _ = go.relax(dt_vd / N, N)
+            t_oscar += time.perf_counter() - t0
+            kfs.append(kf)
+            if full:
+                t0 = time.perf_counter()
+                for _ in range(N):
+                    gp.standard_step(dt_vd / N)
+                t_piso += time.perf_counter() - t0
+                for key, fa, fb in (("alpha", ox.FIELD_ALPHA, ox.FIELD_ALPHA), ("p", ox.FIELD_P, ox.FIELD_P)):
+                    x, y = go.field(fa), gp.field(fb)
+                    err[key] = max(err[key], float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum())))
+                ux = np.hypot(go.field(ox.FIELD_U), go.field(ox.FIELD_U + 1))
+                uy = np.hypot(gp.field(ox.FIELD_U), gp.field(ox.FIELD_U + 1))
+                err["u"] = max(err["u"], float(np.sqrt(((ux - uy) ** 2).sum() / (uy ** 2).sum())))
+        go.close()
+        n_piso = len(kfs) * N
+        if not full:
+            gp = ox.Oscar(p, c.solid, c.alpha0)
+            gp.standard_step(dt_vd / N)          # graph construction
+            t0 = time.perf_counter()
+            for _ in range(piso_sample):
+                gp.standard_step(dt_vd / N)
+            t_piso = (time.perf_counter() - t0) / piso_sample * n_piso
+        gp.close()
+        out["cases"].append({"Ca": Ca, "N": N, "dt_vd": dt_vd, "drag_steps": len(kfs),
+                             "k_f_mean": float(np.mean(kfs)),
+                             "k_f_min": int(min(kfs)), "k_f_max": int(max(kfs)),
+                             "k_f_over_N": float(np.mean(kfs)) / N,
+                             "oscar_s": t_oscar, "oscar_sub_steps": int(sum(kfs)),
+                             "piso_steps": n_piso, "piso_s": t_piso,
+                             "piso_time": "measured" if full else f"extrapolated from {piso_sample} steps",
+                             "speedup": t_piso / t_oscar,
+                             "err_split": max(err.values()) if full else None,
+                             "err_split_fields": err if full else None})
+    return out
+
+
+def film_thickness(alpha, h, W):
+    """Liquid film between a long bubble (alpha = 1) and the channel walls: half
+    the channel width not occupied by the bubble, (W - sum_j alpha h) / 2,
+    averaged over the middle third of the columns the bubble fills more than
+    half of (the flat part of the film)."""
+    b = alpha.sum(axis=0) * h
+    cols = np.where(b > 0.5 * W)[0]
+    if len(cols) < 3:
+        return None
+    i0, i1 = cols[0], cols[-1]
+    L = i1 - i0 + 1
+    mid = np.arange(i0 + L // 3, i1 - L // 3 + 1)
+    return float((W - b[mid].mean()) / 2)
+
+
+def aussillous_quere(Ca, W):
+    """Film thickness of the Aussillous-Quere correlation, h = r 1.34 Ca^(2/3) /
+    (1 + 3.35 Ca^(2/3)) with r = W/2 (the law the paper compares with, Section 5.1)."""
+    x = Ca ** (2.0 / 3.0)
+    return (W / 2) * 1.34 * x / (1 + 3.35 * x)
+
+
+def benchmark1_run(ox, Ca, h, prec, t_frac=1.0, n_smooth=2):
+    """The paper's benchmark 1 (Section 5.1) on the GPU: the bubble is first
+    relaxed towards capillary equilibrium (relaxation sub-steps at 0.99 dt_B,
+    exit at E_k < 1e-4, at most 3000), then ethanol is injected for
+    t* = U t / L = t_frac with dt_vd = 0.01 dt_CFL and dt_cr = dt_vd / N.
+    Returns the final alpha, |u|, p, the film thickness, the bubble velocity
+    over U and the wall seconds of the injection phase."""
+    c = inputs.bubble_film_2d(Ca=Ca, h=h, cg_rtol=1e-10, precision=prec, n_smooth=n_smooth)
+    p = c.params
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+    g = ox.Oscar(p, c.solid, c.alpha0)
+    g.relax(0.99 * dt_b, 3000)
+    n = int(round(t_frac * c.meta["t_end"] / dt_vd))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        g.drag_step(dt_vd)
+        g.relax(dt_vd / N, N)
+    secs = time.perf_counter() - t0
+    a = g.field(ox.FIELD_ALPHA)
+    ux, uy = g.field(ox.FIELD_U), g.field(ox.FIELD_U + 1)
+    pp = g.field(ox.FIELD_P)
+    g.close()
+    W = c.meta["W"]
+    return {"alpha": a, "umag": np.hypot(ux, uy), "p": pp, "film": film_thickness(a, h, W),
+            "bubble_velocity_over_U": float((a * ux).sum() / a.sum()) / p["U_inlet"], "seconds": secs,
+            "drag_steps": n, "N": N, "W": W}
+
+
+def grid_convergence(Ca=1e-2, hs=(1e-6, 2e-6, 5e-6, 10e-6), prec=inputs.PREC_MIXED):
+    """Grid convergence of OSCAR on benchmark 1 (Section 5.1, Table 1): the
+    relative L2 error of Eq. L2 at t* = 1 for the coarser grids against the
+    finest, over beta in (|u|, p, alpha), with the reference averaged onto each
+    coarse grid (the spacings are integer multiples of the finest), plus the
+    film thickness of every grid against the Aussillous-Quere correlation."""
+    from paper_2105_10576_gb300 import oscar as ox
+    runs = {h: benchmark1_run(ox, Ca, h, prec) for h in hs}
+    ref = runs[hs[0]]
+    out = {"workload": f"benchmark 1 (600x100 um, air in ethanol, sigma 0.02), Ca={Ca:g}, t*=1, "
+                       "dt_vd = 0.01 dt_CFL", "Ca": Ca, "film_aq_um": aussillous_quere(Ca, ref["W"]) * 1e6,
+           "grids": []}
+    for h in hs:
+        r = runs[h]
+        row = {"h_um": h * 1e6, "drag_steps": r["drag_steps"], "N": r["N"], "seconds": r["seconds"],
+               "film_um": r["film"] * 1e6 if r["film"] else None,
+               "bubble_velocity_over_U": r["bubble_velocity_over_U"]}
+        if h != hs[0]:
+            f = int(round(h / hs[0]))
+            errs = {}
+            for key in ("umag", "p", "alpha"):
+                x = r[key]
+                y = ref[key].reshape(x.shape[0], f, x.shape[1], f).mean(axis=(1, 3))
+                errs[key] = float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()))
+            row["l2_err"] = max(errs.values())
+            row["l2_err_fields"] = errs
+        out["grids"].append(row)
+    e = [(g["h_um"], g["l2_err"]) for g in out["grids"] if "l2_err" in g and g["l2_err"] > 0]
+    if len(e) >= 2:
+        x, y = np.log([a for a, _ in e]), np.log([b for _, b in e])
+        out["order"] = float(np.polyfit(x, y, 1)[0])
+    return out
+
+
 def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
     """The batched relaxation sweep (config 3): 64 bubble channels, grids drawn
     from {128x16 .. 1024x128}, Ca log-uniform in [1e-6, 1e-3], bubble length
@@ -468,6 +629,9 @@ def main():
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the FP64 run of the same steps that the mixed path is compared with")
     ap.add_argument("--no-tts", action="store_true", help="skip the OSCAR vs standard time-to-solution runs")
+    ap.add_argument("--no-study", action="store_true", help="skip the OSCAR vs standard study across Ca")
+    ap.add_argument("--grid-study", action="store_true",
+                    help="add the grid-convergence and film-thickness study of benchmark 1 (minutes)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-sweep comparison (64 instances)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run (Poisson arrivals)")
     ap.add_argument("--serving-seconds", type=float, default=10.0, help="arrival window of the serving run")
@@ -627,6 +791,12 @@ def main():
     tts = None
     if rank == 0 and not args.no_tts:
         tts = time_to_solution()
+    study = None
+    if rank == 0 and not args.no_study:
+        study = splitting_study()
+    grid = None
+    if rank == 0 and args.grid_study:
+        grid = grid_convergence()
     batched = None
     if rank == 0 and not args.no_batched:
         batched = batched_sweep()
@@ -649,7 +819,7 @@ def main():
                            "device_bytes": int(s_after["device_bytes"])},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "profiled_step": profiled,
-                "precision": precision, "time_to_solution": tts,
+                "precision": precision, "time_to_solution": tts, "splitting_study": study, "grid_convergence": grid,
                 "batched": batched, "serving": serving_res}
         print(json.dumps(line), flush=True)
     if dist is not None:

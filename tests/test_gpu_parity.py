@@ -384,3 +384,105 @@ def test_bench_workload_long_run_stays_bounded():
     v1 = g.stats()["phase_volume"]
     assert v1 - v0 == pytest.approx(p["alpha_inlet"] * inflow, rel=2e-3)
     g.close()
+
+
+def _constriction_fields(c, prec, alpha0, n_steps):
+    p = dict(c.params, precision=prec)
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+    g = ox.Oscar(p, c.solid, alpha0)
+    for _ in range(n_steps):
+        assert g.drag_step(dt_vd) == 0
+        assert g.relax(dt_vd / N, N)[0] == 0
+    f = {"a": g.field(ox.FIELD_ALPHA), "p": g.field(ox.FIELD_P), "u": g.field(ox.FIELD_U)}
+    g.close()
+    return f
+
+
+def test_mixed_precision_against_fp64_on_the_constriction():
+    """Mixed precision against the FP64 GPU path on a reduced 3D constriction
+    (128x32x32, the bench geometry's generator, 10 drag steps of 110 relaxation
+    sub-steps). The integral results the method is used for agree within 0.5 %:
+    the bubble velocity (alpha-weighted mean u_x) and the capillary pressure
+    (mean p where alpha > 0.99 minus where alpha < 0.01); alpha agrees within
+    1e-5 in L1 over the injected volume. Pointwise, alpha is held to four times
+    the spread that a one-ulp FP32 perturbation of alpha0 produces in the mixed
+    run itself (two seeds; at least 1e-5): the capillary dynamics amplify
+    rounding differences (at 256x64x64 such a perturbation moves alpha by 0.1
+    after 10 steps), so no FP32 path can agree pointwise more closely."""
+    c = inputs.constricted_channel_3d(nx=128, ny=32, nz=32, cg_rtol=1e-8)
+    fl = c.solid == 0
+    n = 10
+    ref = _constriction_fields(c, inputs.PREC_FP64, c.alpha0, n)
+    mix = _constriction_fields(c, inputs.PREC_MIXED, c.alpha0, n)
+    spread = 0.0
+    for seed in (0, 1):
+        s = np.random.default_rng(seed).integers(-1, 2, c.alpha0.shape)
+        pert = _constriction_fields(c, inputs.PREC_MIXED, c.alpha0 * (1 + s * 2.0 ** -23), n)
+        spread = max(spread, float(np.abs(pert["a"] - mix["a"])[fl].max()))
+
+    def vb(f):
+        return (f["a"][fl] * f["u"][fl]).sum() / f["a"][fl].sum()
+
+    def pc(f):
+        a, p = f["a"], f["p"]
+        return p[(a > 0.99) & fl].mean() - p[(a < 0.01) & fl].mean()
+
+    assert vb(mix) == pytest.approx(vb(ref), rel=5e-3)
+    assert pc(mix) == pytest.approx(pc(ref), rel=5e-3)
+    da = np.abs(mix["a"] - ref["a"])[fl]
+    assert da.sum() / ref["a"][fl].sum() <= 1e-5
+    assert da.max() <= max(1e-5, 4.0 * spread), (da.max(), spread)
+
+
+def _benchmark1(Ca, prec):
+    """Benchmark 1 of Section 5.1 at 1 um (600x100 cells): relax the initial
+    rectangle towards capillary equilibrium, then inject ethanol up to
+    t* = U t / L = 1 with dt_vd = 0.01 dt_CFL, dt_cr = dt_vd / N."""
+    c = inputs.bubble_film_2d(Ca=Ca, cg_rtol=1e-10, precision=prec)
+    p = c.params
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+    g = ox.Oscar(p, c.solid, c.alpha0)
+    assert g.relax(0.99 * dt_b, 3000)[0] == 0
+    for _ in range(int(round(c.meta["t_end"] / dt_vd))):
+        assert g.drag_step(dt_vd) == 0
+        assert g.relax(dt_vd / N, N)[0] == 0
+    a, ux = g.field(ox.FIELD_ALPHA), g.field(ox.FIELD_U)
+    g.close()
+    W, h = c.meta["W"], p["hx"]
+    b = a.sum(axis=0) * h                 # bubble width per column
+    cols = np.where(b > 0.5 * W)[0]
+    L = cols[-1] - cols[0] + 1
+    mid = np.arange(cols[0] + L // 3, cols[-1] - L // 3 + 1)
+    film = (W - b[mid].mean()) / 2        # flat part of the film, both walls averaged
+    return film, float((a * ux).sum() / a.sum()) / p["U_inlet"], W
+
+
+def _aq(Ca, W):
+    x = Ca ** (2.0 / 3.0)
+    return (W / 2) * 1.34 * x / (1 + 3.35 * x)
+
+
+def test_film_thickness_benchmark1():
+    """The paper's benchmark 1 (Section 5.1; film-thickness figure): the liquid
+    film left by an air bubble driven through a 100 um channel, against the
+    Aussillous-Quere correlation h = r 1.34 Ca^(2/3) / (1 + 3.35 Ca^(2/3)),
+    r = W/2 (2.69 um at Ca = 1e-2; the paper obtains 2.61 um with OSCAR).
+    Checked: the film at Ca = 1e-2 within 25 % of the correlation (measured
+    -20 % with two smoothing passes; the film is 2.7 cells thick and its value
+    moves between 5.1 and 2.2 um with the number of smoothing passes, a
+    quantity the paper does not state); the growth of the film from
+    Ca = 1e-2 to 1e-1 within 20 % of the correlation's ratio (3.1); the bubble
+    velocity equal to the mass-conservation value U W / (W - 2 h) within 2 %;
+    and the mixed path within 0.5 % of the FP64 path in film thickness and
+    bubble velocity at Ca = 1e-2."""
+    h64, v64, W = _benchmark1(1e-2, inputs.PREC_FP64)
+    h32, v32, _ = _benchmark1(1e-2, inputs.PREC_MIXED)
+    h1, v1, _ = _benchmark1(1e-1, inputs.PREC_MIXED)
+    print(f"film Ca=1e-2: FP64 {h64 * 1e6:.3f} um, mixed {h32 * 1e6:.3f} um, AQ {_aq(1e-2, W) * 1e6:.3f} um; "
+          f"Ca=1e-1: {h1 * 1e6:.3f} um, AQ {_aq(1e-1, W) * 1e6:.3f} um")
+    assert h64 == pytest.approx(_aq(1e-2, W), rel=0.25)
+    assert h1 / h64 == pytest.approx(_aq(1e-1, W) / _aq(1e-2, W), rel=0.20)
+    assert v64 == pytest.approx(W / (W - 2 * h64), rel=0.02)
+    assert v1 == pytest.approx(W / (W - 2 * h1), rel=0.02)
+    assert h32 == pytest.approx(h64, rel=5e-3)
+    assert v32 == pytest.approx(v64, rel=5e-3)
