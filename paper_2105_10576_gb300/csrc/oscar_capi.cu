@@ -331,6 +331,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.mg_nu_c = 2;
     I.mg_coarse_sweeps = 4;
     I.mg_nu_cta = 2;
+    I.coarse_refresh = 8;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
@@ -348,6 +349,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
         if (enc && atoi(enc) >= 1 && atoi(enc) <= 4) I.mg_nu_c = atoi(enc);
         const char *ect = getenv("OSCAR_MG_NU_CTA");
         if (ect && atoi(ect) >= 1 && atoi(ect) <= 6) I.mg_nu_cta = atoi(ect);
+        const char *erf = getenv("OSCAR_COARSE_REFRESH");
+        if (erf && atoi(erf) >= 1 && atoi(erf) <= 1000) I.coarse_refresh = atoi(erf);
     }
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];

@@ -23,7 +23,7 @@ enum Slot {
 };
 
 // Integer control words on the device (relaxation and PCG loop state).
-enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COND, C_OUT, C_OSUM, C_COUNT = 12 };
+enum Ctl { C_K = 0, C_N, C_IT, C_ITSUM, C_NAN, C_NOTCONV, C_COND, C_OUT, C_OSUM, C_PACK, C_COUNT = 12 };
 
 // One captured and instantiated step graph.
 struct GraphSlot {
@@ -136,6 +136,7 @@ struct Instance {
     long long cell_updates;
     int mg_nu, mg_nu_c, mg_coarse_sweeps;   // sweeps on the finest level, on coarser levels, on the coarsest
     int mg_nu_cta;         // sweeps on the levels held by the coarse CTA
+    int coarse_refresh;    // the coarsest level's inverse is formed every this many PISO set-ups
     long long nlaunch;     // kernel launches issued by the host (eager or into a capture)
     long long nexec;       // kernels executed on the device (graph executions counted by loop trips)
     Profiler *prof;

@@ -1623,8 +1623,8 @@ template <typename M> struct CLevels {
     int ors;           // residual scratch (cells of the largest level)
     // exact = 1: the coarsest level (at most kExactCells cells) is solved with
     // its explicit inverse, stored row-major at oinv (built by
-    // k_mg_coarse_pack), with chunk partial sums at opart
-    int exact, oinv, opart, nchunk;
+    // k_mg_coarse_pack every refresh-th call, kept in between)
+    int exact, oinv, refresh;
     const M *b_top;    // global b of the top level
     M *x_top;          // global x of the top level
     CLevel<M> L[kMaxCL];
@@ -1652,6 +1652,12 @@ template <> struct CpAsync<8> {
     __device__ static __forceinline__ void copy(void *dst, const void *src) {
         unsigned s = (unsigned)__cvta_generic_to_shared(dst);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(src) : "memory");
+    }
+};
+template <> struct CpAsync<16> {   // both addresses 16-byte aligned; cached in L2 only
+    __device__ static __forceinline__ void copy(void *dst, const void *src) {
+        unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(src) : "memory");
     }
 };
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -1813,24 +1819,18 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
         }
     }
     const CLevel<M> &Lc = P.L[P.n - 1];
-    if (P.exact) {   // x = A^-1 b on the coarsest level: chunked dense product, then the chunk sums
-        const int ne = Lc.g.ncell, per = (ne + P.nchunk - 1) / P.nchunk;
+    if (P.exact) {   // x = A^-1 b on the coarsest level: a warp per row, lanes over the columns
+        const int ne = Lc.g.ncell;
         const M *inv = (const M *)(sm + P.oinv), *bc = (const M *)(sm + Lc.ob);
-        M *part = (M *)(sm + P.opart);
-        __syncthreads();
-        for (int q = t; q < ne * P.nchunk; q += nt) {
-            const int row = q % ne, ch = q / ne;
-            const int j0 = ch * per, j1 = min(ne, j0 + per);
-            M acc = M(0);
-            for (int jj = j0; jj < j1; ++jj) acc += inv[row * ne + jj] * bc[jj];
-            part[ch * ne + row] = acc;
-        }
-        __syncthreads();
         M *xc = (M *)(sm + Lc.ox);
-        for (int q = t; q < ne; q += nt) {
+        __syncthreads();
+        const int lane = t & 31, warp = t >> 5, nwarp = nt >> 5;
+        for (int row = warp; row < ne; row += nwarp) {
             M acc = M(0);
-            for (int ch = 0; ch < P.nchunk; ++ch) acc += part[ch * ne + q];
-            xc[q] = acc;
+            for (int jj = lane; jj < ne; jj += 32) acc += inv[row * ne + jj] * bc[jj];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) xc[row] = acc;
         }
         prev_blk = true;   // the next phase starts with a block barrier
     } else {
@@ -1874,7 +1874,8 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
 // b = 0), built once per set of coefficients (once per PISO set-up) and stored
 // in global memory, so that every V-cycle starts from one contiguous copy
 // instead of redoing the loads and the per-cell rearrangement.
-// With P.exact, the pack also forms the coarsest level's matrix (diagonal d,
+// With P.exact, the pack also forms (on its first call of a step call and
+// every P.refresh-th call after it) the coarsest level's matrix (diagonal d,
 // off-diagonals -w from its per-cell form; rows of cells that are solid or
 // have no coefficients decouple) and inverts it in place by Gauss-Jordan
 // elimination without pivoting (the matrix is symmetric positive definite: the
@@ -1882,12 +1883,22 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
 // fluid pocket cut off from the outlet, whose block is singular) drops its row
 // and column.
 template <int DIM, typename M>
-__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P, uint4 *__restrict__ img, int n16) {
+__global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P, uint4 *__restrict__ img, int n16,
+                                                                   int *__restrict__ ctl) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char sm[];
+    // the inverse is formed on the first call of a step call and on every
+    // refresh-th one after it; in between the stored inverse is kept
+    __shared__ int invert_s;
+    if (threadIdx.x == 0) {
+        const int n = ctl[C_PACK];
+        invert_s = P.exact && (n % P.refresh == 0);
+        ctl[C_PACK] = n + 1;
+    }
     cta_prepare<DIM, M>(P, sm, false);
     __syncthreads();
-    if (P.exact) {
+    const bool invert = invert_s;
+    if (invert) {
         const CLevel<M> &Lc = P.L[P.n - 1];
         const int ne = Lc.g.ncell, t = threadIdx.x, nt = blockDim.x;
         M *A = (M *)(sm + P.oinv);
@@ -1908,37 +1919,63 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P,
                 if (wf != M(0) && nb >= 0 && nb < ne) A[c * ne + nb] = -wf;
             }
         }
-        __shared__ M piv_s;
-        __shared__ int skip_s;
+        // Gauss-Jordan: thread t owns column j = t % ne and the rows g0, g0 + ng,
+        // g0 + 2 ng, ... (g0 = t / ne, ng = nt / ne groups), so a warp touches
+        // consecutive columns of one row (no bank conflicts) and reads the
+        // pivot-column entry of a row as a broadcast. Per pivot: the pivot row
+        // and column entries a thread needs go to registers, a barrier, then
+        // every owned entry gets the rank-one update and the thread fixes up
+        // its entries of the pivot row and column. The single CTA is bound by
+        // instruction issue here (n^3 updates), so the update is one FMA per
+        // entry on a strided pointer. The result is only the coarsest
+        // level's solve inside the preconditioner.
+        // rows per thread: ne / floor(nt / ne) <= 16 for ne <= 128 and nt = 1024
+        constexpr int kRows = (kExactCells * kExactCells + kCtaThreads - 1) / kCtaThreads;
+        static_assert(kRows == 16, "row bound of the Gauss-Jordan mapping");
+        const int ng = nt / ne;
+        const int j = t % ne, g0 = t / ne;
+        const int nrow = t < ng * ne ? (ne - g0 + ng - 1) / ng : 0;   // rows owned
+        const int rs = ng * ne;                                         // stride between them
+        M *const colp = A + g0 * ne + j;
         for (int k = 0; k < ne; ++k) {
             __syncthreads();
-            if (t == 0) {
-                const M pv = A[k * ne + k];
-                skip_s = !(pv > M(0));
-                piv_s = skip_s ? M(0) : M(1) / pv;
-            }
+            const M pv = A[k * ne + k];
+            const bool skip = !(pv > M(0));   // decoupled (or singular) row: zero row and column
+            const M inv = skip ? M(0) : M(1) / pv;
+            M aik[kRows];
+            const M *colk = A + g0 * ne + k;
+#pragma unroll
+            for (int q = 0; q < kRows; ++q) aik[q] = q < nrow ? colk[q * rs] : M(0);
+            const M akj = nrow > 0 ? A[k * ne + j] : M(0);
             __syncthreads();
-            const M inv = piv_s;
-            if (skip_s) {   // decoupled (or singular) row: zero row and column
-                for (int q = t; q < ne; q += nt) { A[k * ne + q] = M(0); A[q * ne + k] = M(0); }
+            if (nrow == 0) continue;
+            const bool own_k = (k - g0) % ng == 0 && k >= g0;   // the pivot row is one of mine
+            const int qk = (k - g0) / ng;
+            if (skip) {
+#pragma unroll
+                for (int q = 0; q < kRows; ++q)
+                    if (q < nrow && j == k) colp[q * rs] = M(0);
+                if (own_k) colp[qk * rs] = M(0);
                 continue;
             }
-            for (int j = t; j < ne; j += nt)
-                if (j != k) A[k * ne + j] *= inv;
-            __syncthreads();
-            for (int q = t; q < ne * ne; q += nt) {
-                const int i = q / ne, j = q - i * ne;
-                if (i == k || j == k) continue;
-                A[q] -= A[i * ne + k] * A[k * ne + j];
+            const M nkj = akj * inv;   // the normalised pivot-row entry
+#pragma unroll
+            for (int q = 0; q < kRows; ++q)
+                if (q < nrow) colp[q * rs] = fma(-aik[q], nkj, colp[q * rs]);
+            if (j == k) {
+#pragma unroll
+                for (int q = 0; q < kRows; ++q)
+                    if (q < nrow) colp[q * rs] = -aik[q] * inv;
             }
-            __syncthreads();
-            for (int i = t; i < ne; i += nt)
-                if (i != k) A[i * ne + k] = -A[i * ne + k] * inv;
-            if (t == 0) A[k * ne + k] = inv;
+            if (own_k) colp[qk * rs] = j == k ? inv : nkj;
         }
         __syncthreads();
     }
-    for (int q = threadIdx.x; q < n16; q += blockDim.x) img[q] = reinterpret_cast<const uint4 *>(sm)[q];
+    // the image, without the inverse's bytes when it was not formed
+    const int q0 = P.exact ? P.oinv / 16 : n16;
+    const int q1 = P.exact ? (P.oinv + P.L[P.n - 1].g.ncell * P.L[P.n - 1].g.ncell * (int)sizeof(M) + 15) / 16 : n16;
+    for (int q = threadIdx.x; q < n16; q += blockDim.x)
+        if (invert || q < q0 || q >= q1) img[q] = reinterpret_cast<const uint4 *>(sm)[q];
 }
 
 // The coarse V-cycle: the image (fixed during a solve) is copied in before the
@@ -1947,7 +1984,9 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P,
 template <int DIM, typename M>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P, const uint4 *__restrict__ img, int n16) {
     extern __shared__ __align__(16) unsigned char sm[];
-    for (int q = threadIdx.x; q < n16; q += blockDim.x) reinterpret_cast<uint4 *>(sm)[q] = img[q];
+    // every 16-byte piece of the image in flight at once (asynchronous copies)
+    for (int q = threadIdx.x; q < n16; q += blockDim.x) CpAsync<16>::copy(sm + 16 * (size_t)q, img + q);
+    cp_async_wait_all();
     griddep_wait();
     M *bt = (M *)(sm + P.L[0].ob);
     for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) bt[q] = P.b_top[q];

@@ -252,7 +252,7 @@ template <typename T> struct Impl {
             CLevels<M> P;
             cta_levels(I, P, I.lc0);
             launchk(k_mg_coarse_pack<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (uint4 *)I.cta_img,
-                    (int)(I.cta_smem / 16)), ++I.nlaunch;
+                    (int)(I.cta_smem / 16), I.ctl), ++I.nlaunch;
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -263,7 +263,8 @@ template <typename T> struct Impl {
     static size_t cta_levels(Instance &I, CLevels<M> &P, int l0, size_t base = 0, bool allow_exact = true) {
         P.n = I.nlev - l0;
         P.exact = 0;
-        P.oinv = P.opart = P.nchunk = 0;
+        P.oinv = 0;
+        P.refresh = I.coarse_refresh;
         if (allow_exact)   // stop at the first level small enough for an exact solve
             for (int q = 0; q < P.n; ++q)
                 if (I.lev[l0 + q].g.ncell <= kExactCells) { P.n = q + 1; P.exact = 1; break; }
@@ -300,9 +301,7 @@ template <typename T> struct Impl {
         P.ors = take(nmax * sizeof(M));
         if (P.exact) {
             const int ne = I.lev[l0 + P.n - 1].g.ncell;
-            P.nchunk = kCtaThreads / ne > 0 ? kCtaThreads / ne : 1;
             P.oinv = take((size_t)ne * ne * sizeof(M));
-            P.opart = take((size_t)P.nchunk * ne * sizeof(M));
         }
         return P.n > kMaxCL ? (size_t)-1 : off;
     }
