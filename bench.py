@@ -112,10 +112,31 @@ def kernel_bytes(name: str, c, e: int):
     return None
 
 
+def kernel_source_sha1(base: str):
+    """SHA-1 of the source text of kernel `base` (from its __global__
+    signature to the closing brace of its body) in oscar_kernels.cuh, or None."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_2105_10576_gb300", "csrc", "oscar_kernels.cuh")
+    try:
+        txt = open(src).read()
+    except OSError:
+        return None
+    m = re.search(r"__global__ void (?:__launch_bounds__\([^)]*\) )?" + re.escape(base) + r"\(", txt)
+    if not m:
+        return None
+    i = txt.index("{", m.end())
+    depth = 0
+    for q in range(i, len(txt)):
+        depth += {"{": 1, "}": -1}.get(txt[q], 0)
+        if depth == 0:
+            return hashlib.sha1(txt[m.start():q + 1].encode()).hexdigest()
+    return None
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of it,
-    or None when there is none or the kernel source changed since the capture."""
-    import hashlib
+    or None when there is none or the kernel's source changed since the capture."""
     files = {"k_mg_rbgs": "k_mg_rbgs_constriction_3d.md", "k_cg_pz_apply": "k_cg_pz_apply_constriction_3d.md",
              "k_cg_update": "k_cg_update_constriction_3d.md",
              "k_mg_resid_restrict": "k_mg_resid_restrict_constriction_3d.md",
@@ -124,12 +145,11 @@ def recorded_traffic(kernel: str):
     if base not in files:
         return None
     path = os.path.join(ROOT, "profiles", files[base])
-    src = os.path.join(ROOT, "paper_2105_10576_gb300", "csrc", "oscar_kernels.cuh")
     try:
         txt = open(path).read()
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
+    sha = kernel_source_sha1(base)
     rec = {}
     for line in txt.splitlines():
         if ":" in line and line.split(":")[0] in ("kernel_source_sha1", "traffic_bytes_per_launch"):
@@ -360,20 +380,34 @@ def splitting_study(cas=(1e-3, 1e-4, 1e-5, 1e-6), n_drag=10, piso_full_max=12000
     run over the same physical time (n_drag N steps) when that is at most
     piso_full_max steps, else its time extrapolated from piso_sample steps (the
     paper extrapolates its slowest PISO runs the same way), and the splitting
-    error of Eq. L2split: the largest over the global steps t_n = n dt_vd and
-    over beta in (|u|, p, alpha) of ||beta_OSCAR - beta_PISO||_2 / ||beta_PISO||_2,
-    with u and p of OSCAR its reconstructed fields (Section 3.2). A Ca whose
+    error of Eq. L2split: the largest over the global steps t_n = n dt_vd,
+    n >= 2, and over beta in (|u|, p, alpha) of ||beta_OSCAR - beta_PISO||_2 /
+    ||beta_PISO||_2, with u and p of OSCAR its reconstructed fields (Section
+    3.2); the first global step is reported apart, since its drag pressure
+    carries the acceleration of the injection started from rest over one
+    drag step (standard stepping spreads it over N steps). A Ca whose
     OSCAR steps pass budget_s seconds stops early; its standard-stepping time
     then covers the drag steps done."""
     from paper_2105_10576_gb300 import oscar as ox
-    out = {"workload": f"2D bubble channel 128x16 over 800x100 um (config 0 geometry and fluids), {n_drag} drag "
-                       "steps at 0.29 dt_CFL, E_k < 1e-4 exit, mixed precision, solves to 1e-8",
+    out = {"workload": f"2D bubble channel 128x16 over 800x100 um (config 0 geometry and fluids), bubble relaxed "
+                       f"towards capillary equilibrium first, {n_drag} drag steps at 0.29 dt_CFL, E_k < 1e-4 exit, "
+                       "mixed precision, solves to 1e-8",
            "cases": []}
+    relaxed = None
     for Ca in cas:
         c = inputs.channel_bubble_2d(Ca=Ca)
         p = dict(c.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8, conv_mode=inputs.CONV_PRES_RESID,
                  conv_tol=1e-4)
         dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, c.meta["c_cfl"], c.solid)
+        if relaxed is None:
+            # both methods start from the bubble relaxed towards capillary
+            # equilibrium (Section 5.1), fluid at rest: relaxation sub-steps at
+            # 0.99 dt_B without injection, exit at E_k < 1e-4 (at most 3000)
+            g0 = ox.Oscar(p, c.solid, c.alpha0)
+            g0.relax(0.99 * dt_b, 3000)
+            relaxed = g0.field(ox.FIELD_ALPHA)
+            g0.close()
+        c.alpha0 = relaxed
         go = ox.Oscar(p, c.solid, c.alpha0)
         n_piso = n_drag * N
         full = n_piso <= piso_full_max
@@ -383,7 +417,9 @@ def splitting_study(cas=(1e-3, 1e-4, 1e-5, 1e-6), n_drag=10, piso_full_max=12000
         go.relax(dt_vd / N, N)
         go.close()
         go = ox.Oscar(p, c.solid, c.alpha0)
-        kfs, t_oscar, t_piso, err = [], 0.0, 0.0, {"alpha": 0.0, "p": 0.0, "u": 0.0}
+        kfs, t_oscar, t_piso = [], 0.0, 0.0
+        err = {"alpha": 0.0, "p": 0.0, "u": 0.0}       # global steps 2 .. n
+        err1 = {"alpha": 0.0, "p": 0.0, "u": 0.0}      # global step 1 (impulsive start of the injection)
         for n in range(n_drag):
             if t_oscar > budget_s:
                 break
@@ -397,12 +433,13 @@ def splitting_study(cas=(1e-3, 1e-4, 1e-5, 1e-6), n_drag=10, piso_full_max=12000
                 for _ in range(N):
                     gp.standard_step(dt_vd / N)
                 t_piso += time.perf_counter() - t0
+                e = err1 if n == 0 else err
                 for key, fa, fb in (("alpha", ox.FIELD_ALPHA, ox.FIELD_ALPHA), ("p", ox.FIELD_P, ox.FIELD_P)):
                     x, y = go.field(fa), gp.field(fb)
-                    err[key] = max(err[key], float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum())))
+                    e[key] = max(e[key], float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum())))
                 ux = np.hypot(go.field(ox.FIELD_U), go.field(ox.FIELD_U + 1))
                 uy = np.hypot(gp.field(ox.FIELD_U), gp.field(ox.FIELD_U + 1))
-                err["u"] = max(err["u"], float(np.sqrt(((ux - uy) ** 2).sum() / (uy ** 2).sum())))
+                e["u"] = max(e["u"], float(np.sqrt(((ux - uy) ** 2).sum() / (uy ** 2).sum())))
         go.close()
         n_piso = len(kfs) * N
         if not full:
@@ -422,7 +459,8 @@ def splitting_study(cas=(1e-3, 1e-4, 1e-5, 1e-6), n_drag=10, piso_full_max=12000
                              "piso_time": "measured" if full else f"extrapolated from {piso_sample} steps",
                              "speedup": t_piso / t_oscar,
                              "err_split": max(err.values()) if full else None,
-                             "err_split_fields": err if full else None})
+                             "err_split_fields": err if full else None,
+                             "err_split_first_step_fields": err1 if full else None})
     return out
 
 
@@ -516,9 +554,11 @@ def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
     2-5 widths (seed 0). A step of an instance is one drag step of 50 dt_cr
     followed by up to 50 relaxation sub-steps of dt_cr = 0.99 dt_Brackbill
     (early exit at max|du_cr|/U < 1e-6), pressure solves to 1e-8. Mixed
-    precision, all instances stepped concurrently (batch.Batch), against the
-    same instances in FP64 stepped one at a time; one untimed warm-up step
-    each (graph construction). Wall-clock seconds through the C ABI."""
+    precision with the solver schedule autotuned per grid size (untimed), all
+    instances stepped concurrently (batch.Batch), against the same instances
+    in FP64 with the default schedule stepped one at a time; one untimed
+    warm-up step each (graph construction). Wall-clock seconds through the C
+    ABI."""
     from paper_2105_10576_gb300 import batch as bt
     from paper_2105_10576_gb300 import oscar as ox
     cases = inputs.batched_sweep(n_inst, seed=0)
@@ -526,6 +566,9 @@ def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
                        f"Ca 1e-6..1e-3; step = drag + up to {n_sub} sub-steps at 0.99 dt_B",
            "unit": UNIT, "steps": steps}
     out = {}
+    from paper_2105_10576_gb300 import autotune
+    tuned = {}
+    t_tune = 0.0
     for mode, prec in (("batched_mixed", inputs.PREC_MIXED), ("sequential_fp64", inputs.PREC_FP64)):
         sims, dtv, dtc = [], [], []
         for c in cases:
@@ -534,6 +577,13 @@ def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
             dtc.append(0.99 * dt_b)
             dtv.append(n_sub * 0.99 * dt_b)
             sims.append(ox.Oscar(p, c.solid, c.alpha0))
+            if mode == "batched_mixed":   # the batch runs the schedule tuned for its grid size
+                key = (p["nx"], p["ny"])
+                if key not in tuned:
+                    t0 = time.perf_counter()
+                    tuned[key] = autotune.tune(p, c.solid, c.alpha0, dtv[-1], dtc[-1], n_sub=n_sub, rounds=1)
+                    t_tune += time.perf_counter() - t0
+                sims[-1].set_schedule(tuned[key])
         nf = [s.stats()["n_fluid"] for s in sims]
         b = bt.Batch(sims)
 
@@ -558,6 +608,8 @@ def batched_sweep(n_inst: int = 64, steps: int = 2, n_sub: int = 50):
         b.close()
     res.update(out)
     res["batched_mixed_over_sequential_fp64"] = out["batched_mixed"]["value"] / out["sequential_fp64"]["value"]
+    res["autotuned_schedules"] = {f"{k[0]}x{k[1]}": v for k, v in tuned.items()}
+    res["autotune_seconds"] = t_tune
     return res
 
 
@@ -626,6 +678,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the profiled (event-bracketed) step")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default solver schedule (no autotuning)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the FP64 run of the same steps that the mixed path is compared with")
     ap.add_argument("--no-tts", action="store_true", help="skip the OSCAR vs standard time-to-solution runs")
@@ -670,7 +723,20 @@ def main():
     nsub = N if args.max_sub <= 0 else min(N, args.max_sub)
     dt_cr = dt_vd / N
     stream = torch.cuda.Stream()
+    tuning = None
+    sched = None
+    if not args.no_tune:
+        # the schedule of the pressure solves, picked by timing candidates on
+        # scratch instances of the same problem (before the timed region)
+        from paper_2105_10576_gb300 import autotune
+        trials = []
+        t0 = time.perf_counter()
+        sched = autotune.tune(p, c.solid, c.alpha0, dt_vd, dt_cr, n_sub=min(nsub, 8), log=trials)
+        tuning = {"seconds": time.perf_counter() - t0, "schedule": sched,
+                  "trials": [{"schedule": s_, "us_per_mcell_update": 1e12 * t_} for s_, t_ in trials]}
     sim = ox.Oscar(p, c.solid, c.alpha0, stream=stream.cuda_stream)
+    if sched is not None:
+        sim.set_schedule(sched)
     st0 = sim.stats()
     nfluid = st0["n_fluid"]
     codes = []
@@ -761,6 +827,8 @@ def main():
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
                         else "fallback"}
 
+    sim_sched = sim.schedule()
+
     # ---- end-to-end through the C ABI with host buffers --------------------
     e2e = None
     if not args.no_e2e:
@@ -814,6 +882,7 @@ def main():
                            "dt_vd": dt_vd, "dt_cr": dt_cr, "N": int(N), "sub_steps_per_step": int(nsub),
                            "k_f": kfs, "step_codes": sorted(set(x for pr in codes for x in pr)),
                            "cg_iters": int(cg_its), "cg_rtol": p["cg_rtol"],
+                           "schedule": sim_sched, "autotune": tuning,
                            "parallelism": f"replicas x{world}",
                            "l2": "working set larger than L2 (no flush needed)",
                            "device_bytes": int(s_after["device_bytes"])},

@@ -192,6 +192,31 @@ int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n);
 /* Statistics of the instance (waits for the stream). */
 int oscar_stats(oscar_handle h, oscar_stats_t *out);
 
+/* Multigrid schedule and launch shape of an instance's pressure solves (not
+ * part of the paper's method, whose solver is unnamed; these choose how fast
+ * the same solves converge, not what they converge to, within cg_rtol).
+ * Defaults at creation: {2, 2, 2, 1024, 8, 0}. */
+typedef struct {
+    int mg_nu;          /* red-black Gauss-Seidel sweep pairs per smoothing step, finest level: 1..4 */
+    int mg_nu_mid;      /* the same on the levels between the finest and the coarse CTA: 1..4 */
+    int mg_nu_cta;      /* the same on the levels held by the single coarse CTA: 1..6 */
+    int cta_cells;      /* levels of at most this many cells (and fitting its shared memory) go to the
+                           coarse CTA: 1..1024 */
+    int coarse_refresh; /* the coarsest CTA level's explicit inverse is formed on the first PISO set-up of
+                           a step call and every coarse_refresh-th after it, kept in between: 1..1000 */
+    int block_x;        /* cap on the x extent of the 256-thread blocks of cell kernels: 0 (none), 32, 64,
+                           128 or 256 */
+} oscar_schedule;
+
+/* Read the schedule of an instance. */
+int oscar_get_schedule(oscar_handle h, oscar_schedule *out);
+
+/* Replace the schedule (waits for the stream; the step graphs are rebuilt at
+ * the next step call). OSCAR_E_INVALID_ARG for a value out of range, while an
+ * asynchronous step is pending, or when the coarse levels chosen by cta_cells
+ * do not fit the coarse CTA's shared memory; the schedule is then unchanged. */
+int oscar_set_schedule(oscar_handle h, const oscar_schedule *s);
+
 /* Release all device memory of the instance. */
 int oscar_destroy(oscar_handle h);
 

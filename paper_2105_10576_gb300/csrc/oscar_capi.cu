@@ -197,6 +197,20 @@ static void carve(Instance &I, Carver &C) {
     I.ticket = (unsigned *)C.take(sizeof(unsigned));
 }
 
+// Partial-sum slots per reduction: the fixed reduction grid, or the blocks
+// of the largest cell launch over every block shape a schedule may select
+// (block_x 32 .. 256; the half-width launches of the red-black sweeps are
+// covered by the full-width count).
+static int reduction_stride(const GridH &g) {
+    long long nb = kRedBlocks;
+    for (int bx = 32; bx <= 256; bx *= 2) {
+        const int by = 256 / bx;
+        const long long b = (long long)((g.nx + bx - 1) / bx) * ((g.ny + by - 1) / by) * g.nz;
+        if (b > nb) nb = b;
+    }
+    return (int)nb;
+}
+
 static int validate(const oscar_params *p) {
     if (!p) return OSCAR_E_INVALID_ARG;
     if (p->dim != 2 && p->dim != 3) return OSCAR_E_INVALID_ARG;
@@ -271,10 +285,7 @@ static void plan(Instance &I, const oscar_params *p) {
     I.prec = p->precision;
     I.g = make_grid(p->dim, p->nx, p->ny, p->nz, p->hx, p->hy, p->hz);
     build_hierarchy(I);
-    int bx = I.g.nx >= 256 ? 256 : (I.g.nx > 64 ? 128 : (I.g.nx > 32 ? 64 : 32));
-    int by = 256 / bx;
-    long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
-    I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
+    I.red_stride = reduction_stride(I.g);
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];
     I.stage_len = stage;
@@ -332,26 +343,15 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.mg_coarse_sweeps = 4;
     I.mg_nu_cta = 2;
     I.coarse_refresh = 8;
+    I.cta_cells = 1024;
+    I.block_x = 0;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
     if (nf == 0) { delete H; return OSCAR_E_INVALID_ARG; }
     build_hierarchy(I);
-    {
-        int bx = I.g.nx >= 256 ? 256 : (I.g.nx > 64 ? 128 : (I.g.nx > 32 ? 64 : 32));
-        int by = 256 / bx;
-        long long nb = (long long)((I.g.nx + bx - 1) / bx) * ((I.g.ny + by - 1) / by) * I.g.nz;
-        I.red_stride = (int)(nb > kRedBlocks ? nb : kRedBlocks);
-        I.lc0 = I.nlev - 1;   // refined by the solver set-up (shared-memory budget of the coarse CTA)
-        const char *enu = getenv("OSCAR_MG_NU");
-        if (enu && atoi(enu) >= 1 && atoi(enu) <= 4) I.mg_nu = atoi(enu);
-        const char *enc = getenv("OSCAR_MG_NUC");
-        if (enc && atoi(enc) >= 1 && atoi(enc) <= 4) I.mg_nu_c = atoi(enc);
-        const char *ect = getenv("OSCAR_MG_NU_CTA");
-        if (ect && atoi(ect) >= 1 && atoi(ect) <= 6) I.mg_nu_cta = atoi(ect);
-        const char *erf = getenv("OSCAR_COARSE_REFRESH");
-        if (erf && atoi(erf) >= 1 && atoi(erf) <= 1000) I.coarse_refresh = atoi(erf);
-    }
+    I.red_stride = reduction_stride(I.g);
+    I.lc0 = I.nlev - 1;   // refined by the solver set-up (shared-memory budget of the coarse CTA)
     size_t stage = I.g.ncell;
     for (int a = 0; a < 3; ++a) if ((size_t)I.g.nf[a] > stage) stage = I.g.nf[a];
     I.stage_len = stage;
@@ -525,6 +525,49 @@ int oscar_set_field(oscar_handle h, int which, const double *host_in, size_t n) 
                               : Solver<float>::field_from_device(I, which, I.stage_dev, len);
     int rc2 = sync_bounded(I.stream, kSyncTimeoutSec);
     return rc ? rc : rc2;
+}
+
+int oscar_get_schedule(oscar_handle h, oscar_schedule *out) {
+    if (!h || !out) return OSCAR_E_INVALID_ARG;
+    const Instance &I = h->I;
+    out->mg_nu = I.mg_nu;
+    out->mg_nu_mid = I.mg_nu_c;
+    out->mg_nu_cta = I.mg_nu_cta;
+    out->cta_cells = I.cta_cells;
+    out->coarse_refresh = I.coarse_refresh;
+    out->block_x = I.block_x;
+    return 0;
+}
+
+int oscar_set_schedule(oscar_handle h, const oscar_schedule *s) {
+    if (!h || !s) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
+    if (s->mg_nu < 1 || s->mg_nu > 4 || s->mg_nu_mid < 1 || s->mg_nu_mid > 4 || s->mg_nu_cta < 1 ||
+        s->mg_nu_cta > 6 || s->cta_cells < 1 || s->cta_cells > 1024 || s->coarse_refresh < 1 ||
+        s->coarse_refresh > 1000)
+        return OSCAR_E_INVALID_ARG;
+    if (!(s->block_x == 0 || s->block_x == 32 || s->block_x == 64 || s->block_x == 128 || s->block_x == 256))
+        return OSCAR_E_INVALID_ARG;
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    const int lc0 = I.lc0;
+    const size_t sm = I.cta_smem;
+    rc = I.prec == OSCAR_FP64 ? Solver<double>::choose_cta(I, s->cta_cells) : Solver<float>::choose_cta(I, s->cta_cells);
+    if (rc) {   // keep the previous schedule
+        I.lc0 = lc0;
+        I.cta_smem = sm;
+        return rc;
+    }
+    I.mg_nu = s->mg_nu;
+    I.mg_nu_c = s->mg_nu_mid;
+    I.mg_nu_cta = s->mg_nu_cta;
+    I.cta_cells = s->cta_cells;
+    I.coarse_refresh = s->coarse_refresh;
+    I.block_x = s->block_x;
+    if (I.prec == OSCAR_FP64) Solver<double>::release_graphs(I);
+    else Solver<float>::release_graphs(I);
+    return 0;
 }
 
 int oscar_stats(oscar_handle h, oscar_stats_t *out) {

@@ -75,6 +75,14 @@ struct Profiler {
 };
 // the profiler of the step being issued on this host thread (null when off)
 inline thread_local Profiler *t_prof = nullptr;
+// cap on the x extent of the thread blocks of cell kernels (0: no cap) of the
+// instance whose launches this host thread is issuing (schedule block_x)
+inline thread_local int t_block_x = 0;
+struct BlockXScope {
+    int saved;
+    explicit BlockXScope(int v) : saved(t_block_x) { t_block_x = v; }
+    ~BlockXScope() { t_block_x = saved; }
+};
 int prof_begin(Profiler *P, cudaStream_t st, const void *fn, dim3 grid, dim3 block);
 void prof_end(Profiler *P, cudaStream_t st, int slot);
 int prof_drain(Profiler *P, cudaStream_t st);
@@ -137,6 +145,8 @@ struct Instance {
     int mg_nu, mg_nu_c, mg_coarse_sweeps;   // sweeps on the finest level, on coarser levels, on the coarsest
     int mg_nu_cta;         // sweeps on the levels held by the coarse CTA
     int coarse_refresh;    // the coarsest level's inverse is formed every this many PISO set-ups
+    int cta_cells;         // levels of at most this many cells go to the coarse CTA
+    int block_x;           // cap on the x extent of cell-kernel blocks (0: none)
     long long nlaunch;     // kernel launches issued by the host (eager or into a capture)
     long long nexec;       // kernels executed on the device (graph executions counted by loop trips)
     Profiler *prof;
@@ -168,6 +178,7 @@ template <typename T> struct Solver {
     static int field_from_device(Instance &I, int which, const double *src, size_t n);
     static int phase_volume(Instance &I, double *out);
     static void release_graphs(Instance &I);
+    static int choose_cta(Instance &I, long long cap);   // first CTA level and its shared memory
 };
 
 int sync_bounded(cudaStream_t s, double timeout_sec);

@@ -91,6 +91,7 @@ struct L3 {
 };
 inline L3 launch3(int nx, int ny, int nz) {
     int bx = nx >= 256 ? 256 : (nx > 64 ? 128 : (nx > 32 ? 64 : 32));
+    if (t_block_x > 0 && t_block_x < bx) bx = t_block_x;   // the instance's schedule caps the x extent
     int by = BS / bx;
     L3 l;
     l.block = dim3(bx, by, 1);

@@ -683,6 +683,7 @@ template <typename T> struct Impl {
     // device scalars back to the host, without waiting
     static bool eager_now(const Instance &I) { return I.eager || (I.prof && I.prof->enabled); }
     static int run_launch(Instance &I, int kind, double dt, int N) {
+        BlockXScope bxs(I.block_x);
         const bool eager = eager_now(I);
         if (!eager) OSCAR_TRY(build(I, kind, dt));
         OSCAR_TRY(sync_bounded(I.stream, kSyncTimeoutSec));   // ctl_host is read by the graph
@@ -746,7 +747,23 @@ template <typename T> void Solver<T>::release_graphs(Instance &I) {
     }
 }
 
+// The coarse CTA takes the levels of at most `cap` cells (at most 1024: one
+// per thread) whose subtree fits the shared-memory budget.
+template <typename T> int Solver<T>::choose_cta(Instance &I, long long cap) {
+    CLevels<T> P;
+    const size_t budget = kCtaImageBytes;
+    if (cap > kCtaCells) cap = kCtaCells;
+    int lc0 = I.nlev - 1;
+    while (lc0 > 0 && I.lev[lc0 - 1].g.ncell <= cap && Impl<T>::cta_levels(I, P, lc0 - 1) <= budget) --lc0;
+    const size_t sm = Impl<T>::cta_levels(I, P, lc0);
+    if (sm > budget) return OSCAR_E_INVALID_ARG;
+    I.lc0 = lc0;
+    I.cta_smem = sm;
+    return 0;
+}
+
 template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev, const double *alpha0_dev) {
+    BlockXScope bxs(I.block_x);
     GridD g = to_dev(I.g);
     L3 L = launch3(I.g);
     long long l0 = I.nlaunch;
@@ -760,17 +777,8 @@ template <typename T> int Solver<T>::setup(Instance &I, const uint8_t *solid_dev
                                                                F.fluid, Lv.fluid), ++I.nlaunch;
     }
     OSCAR_LAUNCH_CHECK();
-    // the coarse CTA takes the levels of at most 1024 cells (one per thread;
-    // larger levels ran faster as separate launches) whose subtree fits the
-    // shared-memory budget; OSCAR_CTA_CELLS moves the cap, for tuning
-    CLevels<T> P;
+    OSCAR_TRY(choose_cta(I, I.cta_cells));
     const size_t budget = kCtaImageBytes;
-    long long cap = 1024;
-    if (const char *e = getenv("OSCAR_CTA_CELLS")) cap = atoll(e) > 0 ? atoll(e) : cap;
-    I.lc0 = I.nlev - 1;
-    while (I.lc0 > 0 && I.lev[I.lc0 - 1].g.ncell <= cap && Impl<T>::cta_levels(I, P, I.lc0 - 1) <= budget) --I.lc0;
-    I.cta_smem = Impl<T>::cta_levels(I, P, I.lc0);
-    if (I.cta_smem > budget) return OSCAR_E_INVALID_ARG;
     // the attribute belongs to the kernel, not to this instance: it is set to
     // the budget (never lowered), so that instances of other sizes, created
     // while this one runs, cannot shrink it below what this one launches with
@@ -850,6 +858,7 @@ static __global__ void k_add_pd(int n, const double *__restrict__ a, const doubl
 }
 
 template <typename T> int Solver<T>::field_to_device(Instance &I, int which, double *dst, size_t n) {
+    BlockXScope bxs(I.block_x);
     int nc = I.g.ncell;
     cudaStream_t s = I.stream;
     auto cvt = [&](const void *src, size_t len) {
@@ -881,6 +890,7 @@ template <typename T> int Solver<T>::field_to_device(Instance &I, int which, dou
 }
 
 template <typename T> int Solver<T>::field_from_device(Instance &I, int which, const double *src, size_t n) {
+    BlockXScope bxs(I.block_x);
     int nc = I.g.ncell;
     cudaStream_t s = I.stream;
     auto cvt = [&](void *dst, size_t len) {
@@ -911,6 +921,7 @@ template <typename T> int Solver<T>::field_from_device(Instance &I, int which, c
 }
 
 template <typename T> int Solver<T>::phase_volume(Instance &I, double *out) {
+    BlockXScope bxs(I.block_x);
     launchk(k_sum_to<T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, (const T *)I.alpha, I.g.V, I.partials, I.ticket, I.scal,
                                                  S_VOL), ++I.nlaunch, ++I.nexec;
     OSCAR_LAUNCH_CHECK();

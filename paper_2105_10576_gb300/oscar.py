@@ -42,6 +42,11 @@ class oscar_params(C.Structure):
     ]
 
 
+class oscar_schedule(C.Structure):
+    _fields_ = [("mg_nu", C.c_int), ("mg_nu_mid", C.c_int), ("mg_nu_cta", C.c_int), ("cta_cells", C.c_int),
+                ("coarse_refresh", C.c_int), ("block_x", C.c_int)]
+
+
 class oscar_stats_t(C.Structure):
     _fields_ = [
         ("k_f", C.c_int), ("N", C.c_int), ("E_last", C.c_double), ("dU_last", C.c_double),
@@ -56,7 +61,7 @@ EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", 
            "oscar_drag_step_async", "oscar_relax_async", "oscar_standard_step_async", "oscar_wait",
            "oscar_footprint", "oscar_query",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
-           "oscar_strerror", "oscar_profile", "oscar_profile_read",
+           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_get_schedule", "oscar_set_schedule",
            "oscar_phase_volume_noalloc"]
 
 _lib = None
@@ -87,6 +92,8 @@ def load(path: str = LIB_PATH):
     lib.oscar_fields_device.argtypes = [H, C.c_int, C.c_void_p, C.c_size_t]
     lib.oscar_set_field.argtypes = [H, C.c_int, dp, C.c_size_t]
     lib.oscar_stats.argtypes = [H, C.POINTER(oscar_stats_t)]
+    lib.oscar_get_schedule.argtypes = [H, C.POINTER(oscar_schedule)]
+    lib.oscar_set_schedule.argtypes = [H, C.POINTER(oscar_schedule)]
     lib.oscar_destroy.argtypes = [H]
     lib.oscar_strerror.argtypes = [C.c_int]
     lib.oscar_strerror.restype = C.c_char_p
@@ -252,6 +259,19 @@ class Oscar:
                    "oscar_profile_read")
             out.append((buf.value.decode(errors="replace"), g.value, ms.value, n.value))
         return out
+
+    def schedule(self) -> dict:
+        """The multigrid schedule and launch shape of the pressure solves."""
+        sc = oscar_schedule()
+        _check(self.lib.oscar_get_schedule(self.h, C.byref(sc)), "oscar_get_schedule")
+        return {name: getattr(sc, name) for name, _ in oscar_schedule._fields_}
+
+    def set_schedule(self, sched: dict):
+        """Replace (some of) the schedule; the step graphs are rebuilt."""
+        cur = self.schedule()
+        cur.update(sched)
+        sc = oscar_schedule(**cur)
+        _check(self.lib.oscar_set_schedule(self.h, C.byref(sc)), "oscar_set_schedule")
 
     def stats(self) -> dict:
         st = oscar_stats_t()

@@ -486,3 +486,36 @@ def test_film_thickness_benchmark1():
     assert v1 == pytest.approx(W / (W - 2 * h1), rel=0.02)
     assert h32 == pytest.approx(h64, rel=5e-3)
     assert v32 == pytest.approx(v64, rel=5e-3)
+
+
+def test_schedule_changes_speed_not_the_solution():
+    """The solver schedule (sweeps per level group, coarse CTA levels, refresh
+    of the coarsest inverse, block shape) changes how the pressure solves
+    converge, not what they converge to: a 3D case stepped with two different
+    schedules agrees within what the solver tolerance allows, a schedule out of
+    range is refused and leaves the instance's schedule unchanged, and the
+    autotuner returns a schedule from its search space."""
+    from paper_2105_10576_gb300 import autotune
+    c = inputs.random_small_case(11, 48, 24, nz=20, dim=3)
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)
+    p = dict(c.params, precision=inputs.PREC_FP64, cg_rtol=1e-13)
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, 0.02)
+    out = []
+    for sched in (dict(autotune.DEFAULT), dict(mg_nu=1, mg_nu_mid=3, mg_nu_cta=1, cta_cells=256,
+                                                coarse_refresh=1, block_x=32)):
+        g = ox.Oscar(p, c.solid, c.alpha0)
+        g.set_schedule(sched)
+        assert g.schedule() == sched
+        g.drag_step(dt_vd)
+        g.relax(dt_vd / N, 3)
+        out.append((g.field(ox.FIELD_ALPHA), g.field(ox.FIELD_P), g.field(ox.FIELD_U)))
+        with pytest.raises(ox.OscarError):
+            g.set_schedule(dict(mg_nu=9))
+        assert g.schedule() == sched
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        assert rel_err(x, y) <= 1e-9
+    best = autotune.tune(dict(p, precision=inputs.PREC_MIXED, cg_rtol=1e-8), c.solid, c.alpha0, dt_vd, dt_vd / N,
+                         n_sub=3, rounds=1, use_cache=False)
+    for name, values in autotune.SPACE:
+        assert best[name] in values
