@@ -306,6 +306,37 @@ __device__ __forceinline__ bool reduce_last(double &v0, double &v1, int nv, bool
     return true;
 }
 
+// reduce_last for up to four FP64 sums (v[0 .. nv), partial slots q * stride),
+// each summed as reduce_last sums one
+__device__ __forceinline__ bool reduce_last4(double *v, int nv, double *__restrict__ part, int stride,
+                                             unsigned *__restrict__ ticket, int nb) {
+    for (int q = 0; q < nv; ++q) v[q] = block_sum(v[q]);
+    __shared__ int last_s;
+    __shared__ double tot_s[4];
+    if (block_leader()) {
+        int b = BLOCK_ID();
+        for (int q = 0; q < nv; ++q) part[q * stride + b] = v[q];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last_s = (t == (unsigned)(nb - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!last_s) return false;
+    __threadfence();
+    int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = tid; b < nb; b += nt)
+        for (int q = 0; q < nv; ++q) s[q] += __ldcg(part + q * stride + b);
+    for (int q = 0; q < nv; ++q) s[q] = block_sum(s[q]);
+    if (block_leader()) {
+        for (int q = 0; q < nv; ++q) tot_s[q] = s[q];
+        *ticket = 0u;
+    }
+    __syncthreads();
+    for (int q = 0; q < nv; ++q) v[q] = tot_s[q];
+    return true;
+}
+
 // reduce_last for one sum of FP32 thread values (compensated block sums,
 // FP64 across blocks); the total is returned in v (all threads of the last
 // block). An FP64 value goes through reduce_last.
@@ -829,35 +860,120 @@ __global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v
     }
 }
 
+// phi* of the face of direction A at face coordinates (i,j,k) (Section 2.2:
+// interior faces (HbyA)_f S + (1/A)_f f_st S with arithmetic face means, the
+// inlet U S, the outlet HbyA_L S, walls 0)
 template <int A, typename T>
-__global__ void k_phistar(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ hbyaA,
-                          const T *__restrict__ rA, const T *__restrict__ fst, T vinA, T *__restrict__ phis) {
-    griddep_wait();
-    FACE_IJK(g, A);
+__device__ __forceinline__ T phistar_face(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
+                                          const T *__restrict__ hbyaA, const T *__restrict__ rA,
+                                          const T *__restrict__ fstA, T vinA) {
     int L, H;
-    int t = decode_face<A>(g, info, i, j, k, L, H);
-    T Sa = GA<T>::S(g, A);
-    T ps = T(0);
-    if (t == FT_INTERIOR) ps = T(0.5) * (hbyaA[L] + hbyaA[H]) * Sa + T(0.5) * (rA[L] + rA[H]) * fst[f] * Sa;
-    else if (t == FT_INLET) ps = vinA * Sa;
-    else if (t == FT_OUTLET) ps = hbyaA[L] * Sa;
-    phis[f] = ps;
+    const int t = decode_face<A>(g, info, i, j, k, L, H);
+    const T Sa = GA<T>::S(g, A);
+    if (t == FT_INTERIOR)
+        return T(0.5) * (hbyaA[L] + hbyaA[H]) * Sa + T(0.5) * (rA[L] + rA[H]) * fstA[flo(g, A, i, j, k)] * Sa;
+    if (t == FT_INLET) return vinA * Sa;
+    if (t == FT_OUTLET) return hbyaA[L] * Sa;
+    return T(0);
 }
 
-// b = -div(phi*), summed in T, stored in FP64
+// phi* of the faces of direction A around cell (i,j,k): its low face is
+// stored (every face is the low face of one cell, or the high face of the
+// last cell of a line), both enter the divergence
+template <int A, typename T>
+__device__ __forceinline__ void phistar_pair(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
+                                             const T *__restrict__ hbyaA, const T *__restrict__ rA,
+                                             const T *__restrict__ fstA, T vinA, T *__restrict__ phisA, T &div) {
+    const T lo = phistar_face<A, T>(g, info, i, j, k, hbyaA, rA, fstA, vinA);
+    const T hi = phistar_face<A, T>(g, info, i + (A == 0), j + (A == 1), k + (A == 2), hbyaA, rA, fstA, vinA);
+    phisA[flo(g, A, i, j, k)] = lo;
+    const int q = A == 0 ? i : (A == 1 ? j : k), n = A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
+    if (q == n - 1) phisA[fhi(g, A, i, j, k)] = hi;
+    div += -lo;
+    div += hi;
+}
+
+// predicted fluxes phi* of every face and the pressure equation's right-hand
+// side b = -div(phi*) in one cell kernel: each face value is computed by both
+// of its cells with the same arithmetic, stored by the cell it is the low face
+// of (or by the last cell of a line), and b sums the low and high faces of
+// every direction in turn
 template <int DIM, typename T>
-__global__ void k_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> phis, double *__restrict__ b) {
+__global__ void k_phistar_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> hbya, const T *__restrict__ rA,
+                              C3<T> fst, T vin0, P3<T> phis, double *__restrict__ b) {
     griddep_wait();
     CELL_IJK(g);
     if (!inside) return;
-    if (!(info[c] & INFO_FLUID)) { b[c] = 0.0; return; }
     T div = T(0);
+    phistar_pair<0, T>(g, info, i, j, k, hbya.a[0], rA, fst.a[0], vin0, phis.a[0], div);
+    phistar_pair<1, T>(g, info, i, j, k, hbya.a[1], rA, fst.a[1], T(0), phis.a[1], div);
+    if constexpr (DIM == 3) phistar_pair<2, T>(g, info, i, j, k, hbya.a[2], rA, fst.a[2], T(0), phis.a[2], div);
+    b[c] = (info[c] & INFO_FLUID) ? (double)(-div) : 0.0;
+}
+
+// corrected flux of the face of direction A at face coordinates (i,j,k):
+// phi = phi* - c_f (q_H - q_L), the pressure difference taken in FP64 (q = 0
+// beyond the outlet face), unchanged on walls and at the inlet
+template <int A, typename T>
+__device__ __forceinline__ T corrected_face(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
+                                            const T *__restrict__ phisA, const T *__restrict__ cfA,
+                                            const double *__restrict__ q) {
+    int L, H;
+    const int t = decode_face<A>(g, info, i, j, k, L, H);
+    const int f = flo(g, A, i, j, k);
+    const T ps = phisA[f];
+    if (t == FT_INTERIOR) return ps - cfA[f] * (T)(q[H] - q[L]);
+    if (t == FT_OUTLET) return ps - cfA[f] * (T)(0.0 - q[L]);
+    return ps;
+}
+
+template <int A, typename T>
+__device__ __forceinline__ void correct_pair(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
+                                             const T *__restrict__ phisA, const T *__restrict__ cfA,
+                                             const double *__restrict__ q, T *__restrict__ phiA) {
+    phiA[flo(g, A, i, j, k)] = corrected_face<A, T>(g, info, i, j, k, phisA, cfA, q);
+    const int qq = A == 0 ? i : (A == 1 ? j : k), n = A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
+    if (qq == n - 1)
+        phiA[fhi(g, A, i, j, k)] = corrected_face<A, T>(g, info, i + (A == 0), j + (A == 1), k + (A == 2), phisA, cfA, q);
+}
+
+// flux correction of every face and velocity correction v = HbyA + (1/A)
+// reconstruct(face accelerations) (Section 2.2) in one cell kernel
+template <int DIM, typename T>
+__global__ void k_correct(GridD g, const uint32_t *__restrict__ info, C3<T> phis, C3<T> cf, const double *__restrict__ q,
+                          P3<T> phi, C3<T> hbya, const T *__restrict__ rA, C3<T> fst, P3<T> v) {
+    griddep_wait();
+    CELL_IJK(g);
+    if (!inside) return;
+    correct_pair<0, T>(g, info, i, j, k, phis.a[0], cf.a[0], q, phi.a[0]);
+    correct_pair<1, T>(g, info, i, j, k, phis.a[1], cf.a[1], q, phi.a[1]);
+    if constexpr (DIM == 3) correct_pair<2, T>(g, info, i, j, k, phis.a[2], cf.a[2], q, phi.a[2]);
+    const uint32_t inf = info[c];
+    if (!(inf & INFO_FLUID)) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) v.a[a][c] = T(0);
+        return;
+    }
+    const double qc = q[c];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        div += -phis.a[a][flo(g, a, i, j, k)];
-        div += phis.a[a][fhi(g, a, i, j, k)];
+        const int off = noff(g, a);
+        const T ha = GA<T>::h(g, a);
+        T gs = T(0);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int t = ftype(inf, a, s);
+            if (t == FT_INTERIOR) {
+                const int nb = s ? c + off : c - off;
+                const int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
+                const double qL = s ? qc : q[nb], qH = s ? q[nb] : qc;
+                gs += fst.a[a][f] - (T)(qH - qL) / ha;
+            } else if (t == FT_OUTLET) {
+                gs += -(T)(0.0 - qc) / (T(0.5) * ha);
+            }
+        }
+        v.a[a][c] = hbya.a[a][c] + rA[c] * T(0.5) * gs;
     }
-    b[c] = (double)(-div);
 }
 
 // (M x)_P = sum_f c_f (x_P - x_N) + sum_outlet c_f x_P, evaluated in type V
@@ -907,39 +1023,6 @@ __device__ __forceinline__ double poisson_row64(const GridD &g, uint32_t inf, in
     return acc;
 }
 
-template <typename T>
-__device__ __forceinline__ double outlet_coeff(const GridD &g, uint32_t inf, int i, int j, int k, C3<T> cf) {
-    return ftype(inf, 0, 1) == FT_OUTLET ? (double)cf.a[0][fhi(g, 0, i, j, k)] : 0.0;
-}
-
-// normalised residual (Section 3.2): res = sum |b - Mq|, nrm = sum |Mq - M qbar| + |b - M qbar|;
-// the finishing block stores E = res / (nrm + 1e-20)
-template <int DIM, typename T>
-__global__ void k_normres(GridD g, const uint32_t *__restrict__ info, C3<T> cf, C3<double> w64,
-                          const double *__restrict__ q,
-                          const double *__restrict__ b, double *__restrict__ scal, double inv_nf,
-                          double *__restrict__ part, int stride, unsigned *__restrict__ ticket, int nb) {
-    griddep_wait();
-    double qbar = scal[S_QSUM] * inv_nf;
-    double res = 0.0, nrm = 0.0;
-    ROW_LOOP(g) {
-        ROW_CELL(g);
-        if (i >= g.nx) continue;
-        uint32_t inf = info[c];
-        if (inf & INFO_FLUID) {
-            double Mq = poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
-            double Mqbar = qbar * outlet_coeff<T>(g, inf, i, j, k, cf);
-            res += fabs(b[c] - Mq);
-            nrm += fabs(Mq - Mqbar) + fabs(b[c] - Mqbar);
-        }
-    }
-    if (reduce_last(res, nrm, 2, false, part, stride, ticket, nb) && block_leader()) {
-        scal[S_RES] = res;
-        scal[S_NRM] = nrm;
-        scal[S_E] = res / (nrm + 1e-20);
-    }
-}
-
 // scal[slot] = scale * sum of x
 template <typename T>
 __global__ void k_sum_to(int n, const T *__restrict__ x, double scale, double *__restrict__ part,
@@ -957,57 +1040,6 @@ __global__ void k_sum_field(int n, const T *__restrict__ x, double scale, double
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) acc += (double)x[c];
     acc = block_sum(acc);
     if (threadIdx.x == 0) part[blockIdx.x] = acc * scale;
-}
-
-// flux correction phi = phi* - c_f (q_H - q_L); the pressure difference is
-// taken in FP64, the rest in T
-template <int A, typename T>
-__global__ void k_flux_correct(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ phis,
-                               const T *__restrict__ cf, const double *__restrict__ q, T *__restrict__ phi) {
-    griddep_wait();
-    FACE_IJK(g, A);
-    int L, H;
-    int t = decode_face<A>(g, info, i, j, k, L, H);
-    T ps = phis[f];
-    T out = ps;
-    if (t == FT_INTERIOR) out = ps - cf[f] * (T)(q[H] - q[L]);
-    else if (t == FT_OUTLET) out = ps - cf[f] * (T)(0.0 - q[L]);
-    phi[f] = out;
-}
-
-// v = HbyA + rA * reconstruct(face accelerations)
-template <int DIM, typename T>
-__global__ void k_vel_correct(GridD g, const uint32_t *__restrict__ info, C3<T> hbya, const T *__restrict__ rA,
-                              C3<T> fst, const double *__restrict__ q, P3<T> v) {
-    griddep_wait();
-    CELL_IJK(g);
-    if (!inside) return;
-    uint32_t inf = info[c];
-    if (!(inf & INFO_FLUID)) {
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) v.a[a][c] = T(0);
-        return;
-    }
-    double qc = q[c];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        int off = noff(g, a);
-        T ha = GA<T>::h(g, a);
-        T gs = T(0);
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            int t = ftype(inf, a, s);
-            if (t == FT_INTERIOR) {
-                int nb = s ? c + off : c - off;
-                int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
-                double qL = s ? qc : q[nb], qH = s ? q[nb] : qc;
-                gs += fst.a[a][f] - (T)(qH - qL) / ha;
-            } else if (t == FT_OUTLET) {
-                gs += -(T)(0.0 - qc) / (T(0.5) * ha);
-            }
-        }
-        v.a[a][c] = hbya.a[a][c] + rA[c] * T(0.5) * gs;
-    }
 }
 
 // u_sum += v and max |v - vold|; the finishing block applies the early exit
@@ -1054,16 +1086,23 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
 // The kernel also starts the first V-cycle: z receives the colour-0 half
 // sweep of the finest level from z = 0 (z = r / diagonal on colour 0, 0 on
 // colour 1), and the Krylov vectors named in zero1 / zero2 (may be null) are
-// cleared. r64 (may be null) receives r in FP64.
+// cleared. r64 (may be null) receives r in FP64. With inv_nf > 0 it also
+// forms the normalised residual of Section 3.2 for the relaxation's exit
+// test: E = sum |b - Mq| / (sum |Mq - M qbar| + sum |b - M qbar| + 1e-20),
+// qbar the mean of q over the fluid cells (scal[S_QSUM] inv_nf), M qbar
+// nonzero only through the outlet coefficients.
 template <int DIM, typename T, typename V>
 __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double> w64, const double *__restrict__ q,
                           const double *__restrict__ b, V *__restrict__ r, double *__restrict__ r64,
                           const V *__restrict__ idiag0, V *__restrict__ z, V *__restrict__ zero1,
                           V *__restrict__ zero2, double *__restrict__ part,
                           int stride, unsigned *__restrict__ ticket, int nb, double *__restrict__ scal,
-                          int *__restrict__ ctl, double rtol, int mode, cudaGraphConditionalHandle h) {
+                          int *__restrict__ ctl, double rtol, int mode, cudaGraphConditionalHandle h,
+                          double inv_nf) {
     griddep_wait();
-    double bb = 0.0, rr = 0.0;
+    const bool with_E = inv_nf > 0.0;
+    const double qbar = with_E ? scal[S_QSUM] * inv_nf : 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // b.b, r.r, sum |b - Mq|, the normalisation
     ROW_LOOP(g) {
         ROW_CELL(g);
         if (i >= g.nx) continue;
@@ -1071,11 +1110,17 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double>
         V rv = V(0);
         double rc = 0.0;
         if (inf & INFO_FLUID) {
-            double bc = b[c];
-            rc = bc - poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
+            const double bc = b[c];
+            const double Mq = poisson_row64<DIM>(g, inf, c, i, j, k, w64, q);
+            rc = bc - Mq;
             rv = (V)rc;
-            bb = fma(bc, bc, bb);
-            rr = fma(rc, rc, rr);
+            acc[0] = fma(bc, bc, acc[0]);
+            acc[1] = fma(rc, rc, acc[1]);
+            if (with_E) {
+                const double Mqbar = ftype(inf, 0, 1) == FT_OUTLET ? qbar * w64.a[0][fhi(g, 0, i, j, k)] : 0.0;
+                acc[2] += fabs(bc - Mq);
+                acc[3] += fabs(Mq - Mqbar) + fabs(bc - Mqbar);
+            }
         }
         r[c] = rv;
         if (r64) r64[c] = rc;
@@ -1083,9 +1128,14 @@ __global__ void k_cg_init(GridD g, const uint32_t *__restrict__ info, C3<double>
         if (zero1) zero1[c] = V(0);
         if (zero2) zero2[c] = V(0);
     }
-    if (reduce_last(bb, rr, 2, false, part, stride, ticket, nb) && block_leader()) {
-        scal[S_BB] = bb;
-        scal[S_RR] = rr;
+    if (reduce_last4(acc, with_E ? 4 : 2, part, stride, ticket, nb) && block_leader()) {
+        scal[S_BB] = acc[0];
+        scal[S_RR] = acc[1];
+        if (with_E) {
+            scal[S_RES] = acc[2];
+            scal[S_NRM] = acc[3];
+            scal[S_E] = acc[2] / (acc[3] + 1e-20);
+        }
         residual_control(scal, ctl, rtol, mode, h);
     }
 }

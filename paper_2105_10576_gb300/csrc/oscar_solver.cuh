@@ -400,14 +400,15 @@ template <typename T> struct Impl {
 
     // r = b - M q (FP64), ||b||^2, ||r||^2 into S_BB, S_RR, then the loop
     // decision of residual_control(mode)
+    // (with_E: also the normalised residual E_k of Section 3.2 for q, b)
     template <int DIM>
     static void residual64(Instance &I, const double *q, const double *b, int mode, cudaGraphConditionalHandle h,
-                           V *zero1, V *zero2, double *r64 = nullptr) {
+                           V *zero1, V *zero2, double *r64 = nullptr, bool with_E = false) {
         GridD g = to_dev(I.g);
         L3 L = launch_rows(I.g, kRedBlocks);
         launchk(k_cg_init<DIM, T, V>, L.grid, L.block, 0, I.stream, g, I.info, w64(I), q, b, (V *)I.cg_r, r64,
                 (const V *)I.lev[0].idiag, (V *)I.cg_z, zero1, zero2, I.partials, I.red_stride, I.ticket, L.nblocks,
-                I.scal, I.ctl, I.P.cg_rtol, mode, h), ++I.nlaunch;
+                I.scal, I.ctl, I.P.cg_rtol, mode, h, with_E ? 1.0 / (double)I.n_fluid : 0.0), ++I.nlaunch;
     }
 
     // one PCG iteration on M x = r with Krylov vectors z, p, Ap (type V)
@@ -444,13 +445,13 @@ template <typename T> struct Impl {
     // Pressure solve M q = b. FP64 path: PCG on q itself. Mixed path: FP64
     // defect correction around an FP32 PCG for the correction e.
     template <int DIM>
-    static int pcg_d(Instance &I, double *q, const double *b) {
+    static int pcg_d(Instance &I, double *q, const double *b, bool with_E) {
         size_t nbytes = (size_t)I.g.ncell * sizeof(V);
         (void)nbytes;
         if constexpr (sizeof(T) == sizeof(double)) {
             cudaGraphConditionalHandle h;
             OSCAR_TRY(cond_handle(I, &h));
-            residual64<DIM>(I, q, b, 0, h, (V *)I.cg_p, nullptr);
+            residual64<DIM>(I, q, b, 0, h, (V *)I.cg_p, nullptr, nullptr, with_E);
             return loop_while(I, h, [&]() -> int { return pcg_body<DIM>(I, (V *)q, S_TARGET, h, 0); });
         } else {
         cudaGraphConditionalHandle ho;
@@ -458,7 +459,7 @@ template <typename T> struct Impl {
         // the inner solve starts e and p from 0 itself (xfresh, beta = 0), so
         // neither is cleared; the FP64 residual is evaluated once, then updated
         // by k_cg_refine at the end of every trip
-        residual64<DIM>(I, q, b, 1, ho, nullptr, nullptr, I.cg_r64);
+        residual64<DIM>(I, q, b, 1, ho, nullptr, nullptr, I.cg_r64, with_E);
         return loop_while(I, ho, [&]() -> int {
             long long n0 = I.nlaunch, cg0 = I.cg_bodies_captured;
             cudaGraphConditionalHandle hi;
@@ -507,34 +508,17 @@ template <typename T> struct Impl {
             launchk(k_momentum_H<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(v), c3(I.vold), c3(I.phic), al,
                                                                    tp(I.rA), fl, (T)vin0, (T)dt, Gc0, Gc1, Gc2,
                                                                    p3(I.hbya)), ++I.nlaunch;
-            launchk(k_phistar<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.hbya[0]), tp(I.rA), tp(I.fst[0]),
-                                                                    (T)vin0, tp(I.phis[0])), ++I.nlaunch;
-            launchk(k_phistar<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.hbya[1]), tp(I.rA), tp(I.fst[1]),
-                                                                    T(0), tp(I.phis[1])), ++I.nlaunch;
-            if (DIM == 3)
-                launchk(k_phistar<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.hbya[2]), tp(I.rA),
-                                                                        tp(I.fst[2]), T(0), tp(I.phis[2])), ++I.nlaunch;
-            launchk(k_rhs<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.phis), I.cg_b), ++I.nlaunch;
-            if (corr == 0) {   // E_k: normalised initial residual of the first corrector (Section 3.2)
+            launchk(k_phistar_rhs<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst),
+                    (T)vin0, p3(I.phis), I.cg_b), ++I.nlaunch;
+            // E_k, the normalised initial residual of the first corrector
+            // (Section 3.2), is formed by the solve's initial-residual kernel
+            if (corr == 0)
                 launchk(k_sum_to<double>, kRedBlocks, BS, 0, I.stream, g.ncell, q, 1.0, I.partials, I.ticket, I.scal,
                                                                   S_QSUM), ++I.nlaunch;
-                L3 LR = launch_rows(I.g, kRedBlocks);
-                launchk(k_normres<DIM, T>, LR.grid, LR.block, 0, I.stream, g, I.info, c3(cf), w64(I), q,
-                        I.cg_b, I.scal,
-                                                                    1.0 / (double)I.n_fluid, I.partials, I.red_stride,
-                                                                    I.ticket, LR.nblocks), ++I.nlaunch;
-            }
             OSCAR_LAUNCH_CHECK();
-            OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b));
-            launchk(k_flux_correct<0, T>, F[0].grid, F[0].block, 0, I.stream, g, I.info, tp(I.phis[0]), tp(cf[0]), q,
-                                                                         tp(phi[0])), ++I.nlaunch;
-            launchk(k_flux_correct<1, T>, F[1].grid, F[1].block, 0, I.stream, g, I.info, tp(I.phis[1]), tp(cf[1]), q,
-                                                                         tp(phi[1])), ++I.nlaunch;
-            if (DIM == 3)
-                launchk(k_flux_correct<2, T>, F[2].grid, F[2].block, 0, I.stream, g, I.info, tp(I.phis[2]), tp(cf[2]), q,
-                                                                             tp(phi[2])), ++I.nlaunch;
-            launchk(k_vel_correct<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.hbya), tp(I.rA), c3(I.fst), q,
-                                                                    p3(v)), ++I.nlaunch;
+            OSCAR_TRY(pcg_d<DIM>(I, q, I.cg_b, corr == 0));
+            launchk(k_correct<DIM, T>, L.grid, L.block, 0, I.stream, g, I.info, c3(I.phis), c3(cf), q, p3(phi),
+                    c3(I.hbya), tp(I.rA), c3(I.fst), p3(v)), ++I.nlaunch;
             OSCAR_LAUNCH_CHECK();
         }
         return 0;
