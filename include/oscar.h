@@ -48,6 +48,10 @@ extern "C" {
 
 #define OSCAR_CONV_PRES_RESID 0 /* E_k: normalised initial residual of PISO corrector 1 (Section 3.2) */
 #define OSCAR_CONV_DU_MAX 1     /* max |u_cr^{k+1} - u_cr^k| / U_inlet */
+#define OSCAR_CONV_AREA 2       /* |E^k - E^{k-1}| / E^{k-1}, E = sigma A + sum rho |u_cr|^2 V / 2 with
+                                   A = sum over fluid cells of |grad alpha| V: the relaxation's energy
+                                   stationary (an energy-balance test of capillary equilibrium, a
+                                   variant suggested in Section 6, not the published method) */
 
 /* Field selectors for oscar_fields / oscar_set_field. */
 #define OSCAR_FIELD_ALPHA 0
@@ -195,7 +199,7 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out);
 /* Multigrid schedule and launch shape of an instance's pressure solves (not
  * part of the paper's method, whose solver is unnamed; these choose how fast
  * the same solves converge, not what they converge to, within cg_rtol).
- * Defaults at creation: {2, 2, 2, 1024, 8, 0}. */
+ * Defaults at creation: {2, 2, 2, 1024, 8, 0, 1}. */
 typedef struct {
     int mg_nu;          /* red-black Gauss-Seidel sweep pairs per smoothing step, finest level: 1..4 */
     int mg_nu_mid;      /* the same on the levels between the finest and the coarse CTA: 1..4 */
@@ -206,6 +210,9 @@ typedef struct {
                            a step call and every coarse_refresh-th after it, kept in between: 1..1000 */
     int block_x;        /* cap on the x extent of the 256-thread blocks of cell kernels: 0 (none), 32, 64,
                            128 or 256 */
+    int cta_global;     /* 1: the level just above the coarse CTA's levels (not the finest) is worked by
+                           the same CTA, its x and b in shared memory and its coefficients read from
+                           global memory, when that fits; 0: by per-level kernels */
 } oscar_schedule;
 
 /* Read the schedule of an instance. */

@@ -90,6 +90,10 @@ def _load():
     lib.or_stage_normalised_residual.restype = C.c_double
     lib.or_stage_normalised_residual.argtypes = [pp, u8p, dp, dp, dp, dp, dp]
     lib.or_stage_piso.argtypes = [pp, u8p] + [dp] * 17 + [C.c_double, C.c_double, dp]
+    lib.or_stage_interface_area.restype = C.c_double
+    lib.or_stage_interface_area.argtypes = [pp, u8p, dp]
+    lib.or_stage_relax_energy.restype = C.c_double
+    lib.or_stage_relax_energy.argtypes = [pp, u8p, dp, dp, dp, dp]
     _lib = lib
     return lib
 
@@ -238,6 +242,27 @@ def stage_interface(p, solid, alpha):
     kap = np.zeros(sh)
     lib.or_stage_interface(C.byref(P), _u8(s), _dp(al), _dp(als), *[_dp(x) for x in n], _dp(kap))
     return als, n[: p["dim"]], kap
+
+
+def stage_interface_area(p, solid, alpha):
+    """Interface area sum |grad alpha| V over fluid cells (Gauss gradient)."""
+    lib = _load()
+    P = make_params(p)
+    sh = grid_shape(p)
+    s = np.ascontiguousarray(solid, np.uint8).reshape(sh)
+    al = np.ascontiguousarray(alpha, np.float64).reshape(sh)
+    return lib.or_stage_interface_area(C.byref(P), _u8(s), _dp(al))
+
+
+def stage_relax_energy(p, solid, alpha, u):
+    """sigma * interface area + kinetic energy of the cell velocities u (list of arrays)."""
+    lib = _load()
+    P = make_params(p)
+    sh = grid_shape(p)
+    s = np.ascontiguousarray(solid, np.uint8).reshape(sh)
+    al = np.ascontiguousarray(alpha, np.float64).reshape(sh)
+    uu = [np.ascontiguousarray(x, np.float64).reshape(sh) for x in u] + [np.zeros(sh)] * (3 - len(u))
+    return lib.or_stage_relax_energy(C.byref(P), _u8(s), _dp(al), *[_dp(x) for x in uu])
 
 
 def stage_poisson_apply(p, solid, cf, q):

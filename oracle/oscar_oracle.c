@@ -38,6 +38,7 @@
 
 #define OR_CONV_PRES_RESID 0
 #define OR_CONV_DU_MAX 1
+#define OR_CONV_AREA 2
 
 /* exact (banded Cholesky) pressure solves up to this many multiply-adds */
 #define OR_BANDED_MAX_WORK 4.0e8
@@ -971,6 +972,39 @@ int or_drag_step(or_state *S, double dt) {
     return po.cg_fail ? -3 : 0;
 }
 
+/* Interface area A = sum over fluid cells of |grad alpha| V, with the Gauss
+ * gradient of alpha (face values: the mean of the two cells on interior faces,
+ * the cell's own value on boundary faces). */
+double or_interface_area(const or_grid *g, const double *alpha) {
+    double A = 0.0;
+    for (int c = 0; c < g->ncell; ++c) {
+        if (g->solid[c]) continue;
+        double m2 = 0.0;
+        for (int b = 0; b < g->dim; ++b) {
+            double gb = gauss_grad_scalar(g, alpha, c, b);
+            m2 += gb * gb;
+        }
+        A += sqrt(m2) * g->V;
+    }
+    return A;
+}
+
+/* Mechanical energy of the relaxation: interfacial energy sigma A plus the
+ * kinetic energy of the capillary velocity, sum over fluid cells of
+ * rho(alpha) |u|^2 V / 2 (Section 2.1 mixture density). Section 6 suggests
+ * identifying capillary equilibrium by an energy balance; the relaxation's
+ * energy test is the relative change of this energy over a sub-step. */
+double or_relax_energy(const or_grid *g, const or_params *P, const double *alpha, double *const *u) {
+    double K = 0.0;
+    for (int c = 0; c < g->ncell; ++c) {
+        if (g->solid[c]) continue;
+        double u2 = 0.0;
+        for (int a = 0; a < g->dim; ++a) u2 += u[a][c] * u[a][c];
+        K += 0.5 * mix_rho(P, alpha[c]) * u2 * g->V;
+    }
+    return P->sigma * or_interface_area(g, alpha) + K;
+}
+
 /* Section 3.2: capillary-relaxation sub-steps (Eqs. VOFc, NSEc, mc) with the
  * early exit on E_k (or on the max velocity change), then the reconstruction
  * of u^{n+1} = u_vd + (1/N) sum_k u_cr^{n,k}. E_hist (may be NULL) receives
@@ -983,6 +1017,7 @@ int or_relax(or_state *S, double dt_cr, int N, int *kf_out, double *E_hist) {
     double vin[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < 3; ++a) memset(S->u_cr_sum[a], 0, nc * sizeof(double));
     int kf = 0, fail = 0;
+    double energy_old = (P->conv_mode == OR_CONV_AREA) ? or_relax_energy(g, P, S->alpha, S->u_cr) : 0.0;
     for (int k = 0; k < N; ++k) {
         or_transport(g, S->alpha, S->phi_cr, S->nf, dt_cr, P->c_alpha, P->alpha_inlet, alpha_new);
         or_interface(g, alpha_new, P->n_smooth, P->theta_deg, S->alpha_s, S->nf, S->kappa);
@@ -1011,6 +1046,11 @@ int or_relax(or_state *S, double dt_cr, int N, int *kf_out, double *E_hist) {
         free_fields(phic); free_fields(vold);
         kf = k + 1;
         double test = (P->conv_mode == OR_CONV_DU_MAX) ? dU : po.E;
+        if (P->conv_mode == OR_CONV_AREA) {   /* relative change of the energy (Section 6) */
+            double energy = or_relax_energy(g, P, S->alpha, S->u_cr);
+            test = fabs(energy - energy_old) / (energy_old > 0.0 ? energy_old : 1.0);
+            energy_old = energy;
+        }
         if (E_hist) E_hist[k] = test;
         S->last_E = po.E;
         S->last_dU = dU;
@@ -1126,6 +1166,20 @@ void or_stage_interface(const or_params *P, const uint8_t *solid, const double *
     grid_init(&g, P, solid);
     double *nf[3] = {nfx, nfy, nfz};
     or_interface(&g, alpha, P->n_smooth, P->theta_deg, alpha_s, nf, kappa);
+}
+
+double or_stage_interface_area(const or_params *P, const uint8_t *solid, const double *alpha) {
+    or_grid g;
+    grid_init(&g, P, solid);
+    return or_interface_area(&g, alpha);
+}
+
+double or_stage_relax_energy(const or_params *P, const uint8_t *solid, const double *alpha, double *ux,
+                             double *uy, double *uz) {
+    or_grid g;
+    grid_init(&g, P, solid);
+    double *u[3] = {ux, uy, uz};
+    return or_relax_energy(&g, P, alpha, u);
 }
 
 void or_stage_poisson_apply(const or_params *P, const uint8_t *solid, double *cx, double *cy, double *cz,

@@ -22,9 +22,9 @@ import time
 
 from . import oscar as ox
 
-DEFAULT = dict(mg_nu=2, mg_nu_mid=2, mg_nu_cta=2, cta_cells=1024, coarse_refresh=8, block_x=0)
+DEFAULT = dict(mg_nu=2, mg_nu_mid=2, mg_nu_cta=2, cta_cells=1024, coarse_refresh=8, block_x=0, cta_global=1)
 SPACE = (("mg_nu", (1, 2, 3)), ("mg_nu_mid", (1, 2, 3)), ("mg_nu_cta", (1, 2, 3)),
-         ("cta_cells", (256, 512, 1024)), ("block_x", (0, 128, 64, 32)))
+         ("cta_cells", (256, 512, 1024)), ("cta_global", (1, 0)), ("block_x", (0, 128, 64, 32)))
 
 _cache: dict = {}
 

@@ -222,7 +222,8 @@ static int validate(const oscar_params *p) {
     if (!(p->rho1 > 0) || !(p->rho2 > 0) || p->mu1 < 0 || p->mu2 < 0 || p->sigma < 0) return OSCAR_E_INVALID_ARG;
     if (p->n_piso < 1 || p->n_smooth < 0 || p->cg_maxit < 1 || !(p->cg_rtol > 0)) return OSCAR_E_INVALID_ARG;
     if (p->precision != OSCAR_FP64 && p->precision != OSCAR_MIXED) return OSCAR_E_INVALID_ARG;
-    if (p->conv_mode != OSCAR_CONV_PRES_RESID && p->conv_mode != OSCAR_CONV_DU_MAX) return OSCAR_E_INVALID_ARG;
+    if (p->conv_mode != OSCAR_CONV_PRES_RESID && p->conv_mode != OSCAR_CONV_DU_MAX && p->conv_mode != OSCAR_CONV_AREA)
+        return OSCAR_E_INVALID_ARG;
     return 0;
 }
 
@@ -345,6 +346,8 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.coarse_refresh = 8;
     I.cta_cells = 1024;
     I.block_x = 0;
+    I.cta_global = 1;
+    I.lg = -1;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
     I.n_fluid = nf;
@@ -536,6 +539,7 @@ int oscar_get_schedule(oscar_handle h, oscar_schedule *out) {
     out->cta_cells = I.cta_cells;
     out->coarse_refresh = I.coarse_refresh;
     out->block_x = I.block_x;
+    out->cta_global = I.cta_global;
     return 0;
 }
 
@@ -549,14 +553,19 @@ int oscar_set_schedule(oscar_handle h, const oscar_schedule *s) {
         return OSCAR_E_INVALID_ARG;
     if (!(s->block_x == 0 || s->block_x == 32 || s->block_x == 64 || s->block_x == 128 || s->block_x == 256))
         return OSCAR_E_INVALID_ARG;
+    if (s->cta_global != 0 && s->cta_global != 1) return OSCAR_E_INVALID_ARG;
     int rc = sync_bounded(I.stream, kSyncTimeoutSec);
     if (rc) return rc;
-    const int lc0 = I.lc0;
-    const size_t sm = I.cta_smem;
+    const int lc0 = I.lc0, lg = I.lg, cg = I.cta_global;
+    const size_t sm = I.cta_smem, ib = I.cta_img_bytes;
+    I.cta_global = s->cta_global;
     rc = I.prec == OSCAR_FP64 ? Solver<double>::choose_cta(I, s->cta_cells) : Solver<float>::choose_cta(I, s->cta_cells);
     if (rc) {   // keep the previous schedule
         I.lc0 = lc0;
+        I.lg = lg;
+        I.cta_global = cg;
         I.cta_smem = sm;
+        I.cta_img_bytes = ib;
         return rc;
     }
     I.mg_nu = s->mg_nu;

@@ -19,7 +19,7 @@ constexpr size_t kCtaImageBytes = 224 * 1024;   // shared-memory budget of the c
 // Scalar slots in the device scalar array (double).
 enum Slot {
     S_BB = 0, S_RR, S_RZ0, S_RZ1, S_PAP, S_QSUM, S_RES, S_NRM, S_DUMAX, S_VOL, S_TARGET, S_E, S_DU, S_TEST,
-    S_ITARGET, S_ALPHA, S_BETA, S_ALPHA_F, S_BETA_F, S_TMP, S_COUNT
+    S_ITARGET, S_ALPHA, S_BETA, S_ALPHA_F, S_BETA_F, S_TMP, S_AREA0, S_AREA1, S_COUNT
 };
 
 // Integer control words on the device (relaxation and PCG loop state).
@@ -125,6 +125,8 @@ struct Instance {
     int red_stride;        // partials per slot: max(kRedBlocks, blocks of a cell launch)
     int lc0;               // first multigrid level solved by the single-CTA coarse kernel
     size_t cta_smem;       // shared memory of the coarse kernel
+    size_t cta_img_bytes;  // bytes of the coarse levels' image (the start of that shared memory)
+    int lg;                // level worked by the coarse CTA with global coefficients, -1 when none
     void *cta_img;         // shared-memory image of the coarse levels (kCtaImageBytes, built per PISO set-up)
     int pending;           // kind (0 drag, 1 relax, 2 standard) of a launched step not yet waited for, or -1
     double pending_dt;
@@ -147,6 +149,7 @@ struct Instance {
     int coarse_refresh;    // the coarsest level's inverse is formed every this many PISO set-ups
     int cta_cells;         // levels of at most this many cells go to the coarse CTA
     int block_x;           // cap on the x extent of cell-kernel blocks (0: none)
+    int cta_global;        // 1: the level above the CTA's may go to the CTA with global coefficients
     long long nlaunch;     // kernel launches issued by the host (eager or into a capture)
     long long nexec;       // kernels executed on the device (graph executions counted by loop trips)
     Profiler *prof;

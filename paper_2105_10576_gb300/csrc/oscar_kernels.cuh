@@ -692,6 +692,36 @@ __global__ void k_curvature(GridD g, const uint32_t *__restrict__ info, C3<T> nf
 template <typename T> struct Fluid { T rho1, rho2, mu1, mu2; };
 template <typename T> __device__ __forceinline__ T mix(T al, T p1, T p2) { return al * p1 + (T(1) - al) * p2; }
 
+// Mechanical energy of the relaxation: the interfacial energy sigma A, with
+// A = sum over fluid cells of |grad alpha| V (Gauss gradient, boundary faces
+// take the cell's value), plus the kinetic energy sum of rho(alpha) |u|^2 V / 2.
+// The finishing block stores it in scal[slot]. Section 6 suggests identifying
+// capillary equilibrium by an energy balance; the relaxation's
+// OSCAR_CONV_AREA mode exits when this energy changes by less than the
+// tolerance (relative) over a sub-step.
+template <int DIM, typename T>
+__global__ void k_relax_energy(int n, GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha,
+                               C3<T> u, Fluid<T> fl, double sigma, double *__restrict__ part, int stride,
+                               unsigned *__restrict__ ticket, double *__restrict__ scal, int slot) {
+    griddep_wait();
+    double area = 0.0, kin = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        if (!(info[c] & INFO_FLUID)) continue;
+        T m2 = T(0), u2 = T(0);
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) {
+            const T gb = gauss_grad<DIM, T>(g, info, alpha, c, b);
+            m2 += gb * gb;
+            const T ub = u.a[b][c];
+            u2 += ub * ub;
+        }
+        area += (double)sqrt(m2) * g.V;
+        kin += 0.5 * (double)mix(alpha[c], fl.rho1, fl.rho2) * (double)u2 * g.V;
+    }
+    if (reduce_last(area, kin, 2, false, part, stride, ticket, gridDim.x) && block_leader())
+        scal[slot] = sigma * area + kin;
+}
+
 // rA = 1/A, A = rho/dt + (viscous diagonal + rho * inflow flux)/V
 template <int DIM, typename T>
 __global__ void k_rA(GridD g, const uint32_t *__restrict__ info, const T *__restrict__ alpha, C3<T> phic, Fluid<T> fl,
@@ -1068,6 +1098,11 @@ __global__ void k_relax_accum(int n, const uint32_t *__restrict__ info, C3<T> v,
         double E = scal[S_E];
         double dU = m * invU;
         double test = mode == OSCAR_CONV_DU_MAX ? dU : E;
+        if (mode == OSCAR_CONV_AREA) {   // relative change of the relaxation's energy in this sub-step
+            const double a0 = scal[S_AREA0], a1 = scal[S_AREA1];
+            test = fabs(a1 - a0) / (a0 > 0.0 ? a0 : 1.0);
+            scal[S_AREA0] = a1;
+        }
         scal[S_DU] = dU;
         scal[S_TEST] = test;
         bool bad = !isfinite(test) || ctl[C_NAN];
@@ -1657,6 +1692,7 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
 // level); the residual for the restriction is formed cell-parallel first.
 constexpr int kCtaThreads = 1024;
 constexpr int kExactCells = 128;   // coarsest CTA level solved exactly when at most this size
+constexpr int kGlCells = 16384;    // largest level the CTA works with global coefficients
 template <typename M> struct CLevel {
     GridD g;
     const M *c[3];          // global face coefficients
@@ -1669,7 +1705,27 @@ template <typename M> struct CLevel {
     // lists, fluid flags, staging of the face arrays
     int ox, ob, od, oi, ow, opk, ol[2], ofl, os[3];
 };
+// The level just above the coarse CTA's levels, worked by the same CTA with
+// its x and b in shared memory and its coefficients, diagonal, inverse
+// diagonal and fluid flags read from global memory (the level is too large for
+// the per-cell form, small enough for its x and b). Same operations as the
+// per-level kernels: red-black sweeps from x = 0, residual and restriction
+// into the CTA's first level, prolongation, reverse-order sweeps.
+template <typename M> struct GLevel {
+    int active;
+    GridD g;
+    MG3<M> c;                  // face coefficients
+    const M *diag, *idiag;
+    const uint8_t *fluid;
+    int r[3];                  // ratios to the CTA's first level
+    float rhx, rny;            // 1/ceil(nx/2), 1/ny (colour-cell decomposition)
+    int ox, ob;                // shared-memory byte offsets of x and b
+    int nu;                    // sweep pairs per smoothing step
+    const M *b_glob;           // b of the level (written by the preceding restriction)
+    M *x_glob;                 // x of the level after the post-smoothing
+};
 template <typename M> struct CLevels {
+    GLevel<M> G;
     int n, nu, nu_top, coarse_sweeps;
     int ors;           // residual scratch (cells of the largest level)
     // exact = 1: the coarsest level (at most kExactCells cells) is solved with
@@ -1921,6 +1977,63 @@ __device__ __forceinline__ void cta_vcycle(const CLevels<M> &P, unsigned char *s
     __syncthreads();
 }
 
+// one colour of a red-black sweep of the global-coefficient level (threads t0, t0 + st, ...)
+template <int DIM, typename M>
+__device__ __forceinline__ void gl_sweep(const GLevel<M> &G, unsigned char *sm, int colour) {
+    M *x = (M *)(sm + G.ox);
+    const M *b = (const M *)(sm + G.ob);
+    const int hx = (G.g.nx + 1) >> 1, nh = hx * G.g.ny * G.g.nz;
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        int ti, j, k;
+        split3(h, hx, G.rhx, G.g.ny, G.rny, ti, j, k);
+        const int i = 2 * ti + ((j + k + colour) & 1);
+        if (i >= G.g.nx) continue;
+        const int cell = i + G.g.nx * (j + G.g.ny * k);
+        M w[2 * DIM];
+        mg_row_coeffs<DIM, M>(G.g, G.c, i, j, k, w);
+        x[cell] = (b[cell] + mg_row_off<DIM, M>(G.g, w, x, cell, i, j, k)) * G.idiag[cell];
+    }
+}
+
+// b of the CTA's first level C = the sum over its children of the fluid
+// residual b - (diag x - off) of the global-coefficient level
+template <int DIM, typename M>
+__device__ __forceinline__ void gl_restrict(const GLevel<M> &G, const CLevel<M> &C, unsigned char *sm) {
+    const M *x = (const M *)(sm + G.ox), *b = (const M *)(sm + G.ob);
+    M *bc = (M *)(sm + C.ob);
+    const uint32_t *pkc = (const uint32_t *)(sm + C.opk);
+    for (int q = threadIdx.x; q < C.g.ncell; q += blockDim.x) {
+        int I, J, K;
+        pk_ijk(pkc[q], I, J, K);
+        const int i0 = I * G.r[0], j0 = J * G.r[1], k0 = K * G.r[2];
+        const int i1 = min(i0 + G.r[0], G.g.nx), j1 = min(j0 + G.r[1], G.g.ny), k1 = min(k0 + G.r[2], G.g.nz);
+        M acc = M(0);
+        for (int kk = k0; kk < k1; ++kk)
+            for (int jj = j0; jj < j1; ++jj)
+                for (int ii = i0; ii < i1; ++ii) {
+                    const int cell = ii + G.g.nx * (jj + G.g.ny * kk);
+                    if (!G.fluid[cell]) continue;
+                    M w[2 * DIM];
+                    mg_row_coeffs<DIM, M>(G.g, G.c, ii, jj, kk, w);
+                    acc += b[cell] - (G.diag[cell] * x[cell] - mg_row_off<DIM, M>(G.g, w, x, cell, ii, jj, kk));
+                }
+        bc[q] = acc;
+    }
+}
+
+// x += the piecewise-constant prolongation of the CTA's first level's x
+template <int DIM, typename M>
+__device__ __forceinline__ void gl_prolong(const GLevel<M> &G, const CLevel<M> &C, unsigned char *sm) {
+    M *x = (M *)(sm + G.ox);
+    const M *xc = (const M *)(sm + C.ox);
+    const int s0 = G.r[0] >> 1, s1 = G.r[1] >> 1, s2 = G.r[2] >> 1;
+    for (int q = threadIdx.x; q < G.g.ncell; q += blockDim.x) {
+        int i, j, k;
+        split3(q, G.g.nx, 1.0f / (float)G.g.nx, G.g.ny, G.rny, i, j, k);
+        x[q] += xc[(i >> s0) + C.g.nx * ((j >> s1) + C.g.ny * (k >> s2))];
+    }
+}
+
 // The shared-memory image of the coarse levels (cta_prepare with x = 0 and
 // b = 0), built once per set of coefficients (once per PISO set-up) and stored
 // in global memory, so that every V-cycle starts from one contiguous copy
@@ -2032,18 +2145,52 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse_pack(CLevels<M> P,
 // The coarse V-cycle: the image (fixed during a solve) is copied in before the
 // grid-dependency wait, then b of the top level, written by the preceding
 // restriction, after it.
+// With P.G.active the CTA first pre-smooths the global-coefficient level and
+// restricts its residual into its first level, and after that level's
+// V-cycle prolongates back and post-smooths (see GLevel).
 template <int DIM, typename M>
 __global__ void __launch_bounds__(kCtaThreads, 1) k_mg_coarse(CLevels<M> P, const uint4 *__restrict__ img, int n16) {
     extern __shared__ __align__(16) unsigned char sm[];
     // every 16-byte piece of the image in flight at once (asynchronous copies)
     for (int q = threadIdx.x; q < n16; q += blockDim.x) CpAsync<16>::copy(sm + 16 * (size_t)q, img + q);
     cp_async_wait_all();
+    const GLevel<M> &G = P.G;
+    if (G.active) {   // x of the level starts at 0
+        M *gx = (M *)(sm + G.ox);
+        for (int q = threadIdx.x; q < G.g.ncell; q += blockDim.x) gx[q] = M(0);
+    }
     griddep_wait();
-    M *bt = (M *)(sm + P.L[0].ob);
-    for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) bt[q] = P.b_top[q];
+    if (G.active) {
+        M *gb = (M *)(sm + G.ob);
+        for (int q = threadIdx.x; q < G.g.ncell; q += blockDim.x) gb[q] = G.b_glob[q];
+        for (int s = 0; s < G.nu; ++s) {
+            __syncthreads();
+            gl_sweep<DIM, M>(G, sm, 0);
+            __syncthreads();
+            gl_sweep<DIM, M>(G, sm, 1);
+        }
+        __syncthreads();
+        gl_restrict<DIM, M>(G, P.L[0], sm);
+    } else {
+        M *bt = (M *)(sm + P.L[0].ob);
+        for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) bt[q] = P.b_top[q];
+    }
     __syncthreads();
     cta_vcycle<DIM, M>(P, sm);
-    for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) P.x_top[q] = ((const M *)(sm + P.L[0].ox))[q];
+    if (G.active) {
+        gl_prolong<DIM, M>(G, P.L[0], sm);
+        for (int s = 0; s < G.nu; ++s) {
+            __syncthreads();
+            gl_sweep<DIM, M>(G, sm, 1);
+            __syncthreads();
+            gl_sweep<DIM, M>(G, sm, 0);
+        }
+        __syncthreads();
+        const M *gx = (const M *)(sm + G.ox);
+        for (int q = threadIdx.x; q < G.g.ncell; q += blockDim.x) G.x_glob[q] = gx[q];
+    } else {
+        for (int q = threadIdx.x; q < P.L[0].g.ncell; q += blockDim.x) P.x_top[q] = ((const M *)(sm + P.L[0].ox))[q];
+    }
 }
 
 }  // namespace oscar

@@ -251,8 +251,8 @@ template <typename T> struct Impl {
         {   // the coarse CTA's shared-memory image for this set of coefficients
             CLevels<M> P;
             cta_levels(I, P, I.lc0);
-            launchk(k_mg_coarse_pack<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (uint4 *)I.cta_img,
-                    (int)(I.cta_smem / 16), I.ctl), ++I.nlaunch;
+            launchk(k_mg_coarse_pack<DIM, M>, 1, kCtaThreads, I.cta_img_bytes, I.stream, P, (uint4 *)I.cta_img,
+                    (int)(I.cta_img_bytes / 16), I.ctl), ++I.nlaunch;
         }
         OSCAR_LAUNCH_CHECK();
         return 0;
@@ -261,6 +261,7 @@ template <typename T> struct Impl {
     // levels l0.. of the single-CTA coarse kernel with their shared-memory
     // layout; returns the bytes of shared memory they need
     static size_t cta_levels(Instance &I, CLevels<M> &P, int l0, size_t base = 0, bool allow_exact = true) {
+        memset(&P.G, 0, sizeof(P.G));
         P.n = I.nlev - l0;
         P.exact = 0;
         P.oinv = 0;
@@ -304,6 +305,30 @@ template <typename T> struct Impl {
             P.oinv = take((size_t)ne * ne * sizeof(M));
         }
         return P.n > kMaxCL ? (size_t)-1 : off;
+    }
+
+    // the global-coefficient level lg of the coarse CTA, its x and b placed in
+    // shared memory after the image of the CTA's levels
+    static void gl_fill(Instance &I, CLevels<M> &P, int lg) {
+        GLevel<M> &G = P.G;
+        const Level &L = I.lev[lg];
+        G.active = 1;
+        G.g = to_dev(L.g);
+        G.c = mg3(L);
+        G.diag = (const M *)L.diag;
+        G.idiag = (const M *)L.idiag;
+        G.fluid = L.fluid;
+        for (int a = 0; a < 3; ++a) G.r[a] = L.r[a];
+        G.rhx = 1.0f / (float)((L.g.nx + 1) / 2);
+        G.rny = 1.0f / (float)L.g.ny;
+        const size_t base = (I.cta_img_bytes + 15) & ~(size_t)15;
+        G.ox = (int)base;
+        G.ob = (int)(base + (((size_t)L.g.ncell * sizeof(M) + 15) & ~(size_t)15));
+        G.nu = I.mg_nu_c;
+    }
+    static size_t gl_bytes(const Instance &I, int lg, size_t img) {
+        const size_t n = (size_t)I.lev[lg].g.ncell * sizeof(M);
+        return ((img + 15) & ~(size_t)15) + 2 * ((n + 15) & ~(size_t)15);
     }
 
     // x / b of level l (level 0 works in place on the Krylov vectors z / r)
@@ -366,7 +391,7 @@ template <typename T> struct Impl {
     // k_cg_update for the finest level, the restriction for the others).
     template <int DIM>
     static int vcycle_d(Instance &I, V *r, V *z) {
-        const int lk = I.lc0;   // first level not worked by per-level kernels
+        const int lk = I.lg >= 0 ? I.lg : I.lc0;   // first level not worked by per-level kernels
         for (int l = 0; l < lk; ++l) {
             Level &L = I.lev[l], &C = I.lev[l + 1];
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -382,8 +407,13 @@ template <typename T> struct Impl {
             cta_levels(I, P, I.lc0);
             P.b_top = lb(I, I.lc0, r);
             P.x_top = lx(I, I.lc0, z);
+            if (I.lg >= 0) {
+                gl_fill(I, P, I.lg);
+                P.G.b_glob = lb(I, I.lg, r);
+                P.G.x_glob = lx(I, I.lg, z);
+            }
             launchk(k_mg_coarse<DIM, M>, 1, kCtaThreads, I.cta_smem, I.stream, P, (const uint4 *)I.cta_img,
-                    (int)(I.cta_smem / 16)), ++I.nlaunch;
+                    (int)(I.cta_img_bytes / 16)), ++I.nlaunch;
         }
         for (int l = lk - 1; l >= 0; --l) {
             M *x = lx(I, l, z), *b = lb(I, l, r);
@@ -541,6 +571,19 @@ template <typename T> struct Impl {
         OSCAR_LAUNCH_CHECK();
         return 0;
     }
+    // scal[slot] = sigma A + kinetic energy of u_cr (the energy exit test)
+    static int relax_energy(Instance &I, int slot) {
+        GridD g = to_dev(I.g);
+        Fluid<T> fl{(T)I.P.rho1, (T)I.P.rho2, (T)I.P.mu1, (T)I.P.mu2};
+        if (I.g.dim == 3)
+            launchk(k_relax_energy<3, T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, g, I.info, (const T *)I.alpha,
+                    c3(I.u_cr), fl, I.P.sigma, I.partials, I.red_stride, I.ticket, I.scal, slot), ++I.nlaunch;
+        else
+            launchk(k_relax_energy<2, T>, kRedBlocks, BS, 0, I.stream, I.g.ncell, g, I.info, (const T *)I.alpha,
+                    c3(I.u_cr), fl, I.P.sigma, I.partials, I.red_stride, I.ticket, I.scal, slot), ++I.nlaunch;
+        OSCAR_LAUNCH_CHECK();
+        return 0;
+    }
     static int commit_alpha(Instance &I) {
         return cudaMemcpyAsync(I.alpha, I.alpha_new, (size_t)I.g.ncell * sizeof(T), cudaMemcpyDeviceToDevice,
                                I.stream) == cudaSuccess ? 0 : OSCAR_E_CUDA;
@@ -584,6 +627,8 @@ template <typename T> struct Impl {
                 return OSCAR_E_CUDA;
         cudaGraphConditionalHandle h;
         OSCAR_TRY(cond_handle(I, &h));
+        const bool area = I.P.conv_mode == OSCAR_CONV_AREA;
+        if (area) OSCAR_TRY(relax_energy(I, S_AREA0));
         launchk(k_relax_init, 1, 1, 0, I.stream, I.ctl, h), ++I.nlaunch;
         *n_pre = I.nlaunch - s0;
         long long b0 = I.nlaunch, cg0 = I.cg_bodies_captured;
@@ -600,6 +645,7 @@ template <typename T> struct Impl {
             OSCAR_TRY(piso(I, I.u_cr, I.p_cr, I.phi_cr, true, 0.0, dt));
             npiso_solves += I.P.n_piso;
             OSCAR_TRY(commit_alpha(I));
+            if (area) OSCAR_TRY(relax_energy(I, S_AREA1));
             P3<double> us;
             for (int a = 0; a < 3; ++a) us.a[a] = I.u_sum[a];
             double invU = I.P.U_inlet > 0 ? 1.0 / I.P.U_inlet : 0.0;
@@ -742,7 +788,19 @@ template <typename T> int Solver<T>::choose_cta(Instance &I, long long cap) {
     const size_t sm = Impl<T>::cta_levels(I, P, lc0);
     if (sm > budget) return OSCAR_E_INVALID_ARG;
     I.lc0 = lc0;
-    I.cta_smem = sm;
+    I.cta_img_bytes = (sm + 15) & ~(size_t)15;
+    I.cta_smem = I.cta_img_bytes;
+    I.lg = -1;
+    // the level above may join the CTA with its coefficients in global memory
+    // when its x and b fit beside the image (never the finest level, whose x
+    // and b are the Krylov vectors of the CG kernels)
+    if (I.cta_global && lc0 - 1 >= 1 && I.lev[lc0 - 1].g.ncell <= kGlCells) {
+        const size_t tot = Impl<T>::gl_bytes(I, lc0 - 1, I.cta_img_bytes);
+        if (tot <= budget) {
+            I.lg = lc0 - 1;
+            I.cta_smem = tot;
+        }
+    }
     return 0;
 }
 

@@ -29,6 +29,7 @@ import numpy as np
 # Convergence-test modes (mirrors include/oscar.h).
 CONV_PRES_RESID = 0   # normalised initial residual of the 1st PISO pressure equation (Section 3.2)
 CONV_DU_MAX = 1       # max |u_cr^{k+1} - u_cr^k| / U_inlet
+CONV_AREA = 2         # relative change of sigma * area + kinetic energy per sub-step (Section 6 variant)
 
 PREC_FP64 = 0
 PREC_MIXED = 1

@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "liboscar_gb300.so")
 
 OSCAR_FP64, OSCAR_MIXED = 0, 1
-CONV_PRES_RESID, CONV_DU_MAX = 0, 1
+CONV_PRES_RESID, CONV_DU_MAX, CONV_AREA = 0, 1, 2
 FIELD_ALPHA, FIELD_P, FIELD_U, FIELD_U_VD, FIELD_U_CR = 0, 1, 2, 5, 8
 FIELD_P_VD, FIELD_P_CR, FIELD_KAPPA, FIELD_PHI_VD, FIELD_PHI_CR, FIELD_NF = 11, 12, 13, 14, 17, 20
 
@@ -44,7 +44,7 @@ class oscar_params(C.Structure):
 
 class oscar_schedule(C.Structure):
     _fields_ = [("mg_nu", C.c_int), ("mg_nu_mid", C.c_int), ("mg_nu_cta", C.c_int), ("cta_cells", C.c_int),
-                ("coarse_refresh", C.c_int), ("block_x", C.c_int)]
+                ("coarse_refresh", C.c_int), ("block_x", C.c_int), ("cta_global", C.c_int)]
 
 
 class oscar_stats_t(C.Structure):

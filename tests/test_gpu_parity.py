@@ -519,3 +519,46 @@ def test_schedule_changes_speed_not_the_solution():
                          n_sub=3, rounds=1, use_cache=False)
     for name, values in autotune.SPACE:
         assert best[name] in values
+
+
+def test_coarse_cta_with_global_level_is_the_same_vcycle():
+    """The level above the coarse CTA's levels worked by the CTA itself (x and
+    b in shared memory, coefficients from global memory) performs the same
+    operations as the per-level kernels: the fields after a drag step and
+    relaxation sub-steps are bitwise equal with and without it (mixed path,
+    3D grid whose 2880-cell level qualifies)."""
+    c = inputs.random_small_case(12, 48, 24, nz=20, dim=3)
+    c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)
+    p = dict(c.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, 0.02)
+    out = []
+    for flag in (1, 0):
+        g = ox.Oscar(p, c.solid, c.alpha0)
+        g.set_schedule(dict(cta_global=flag))
+        g.drag_step(dt_vd)
+        g.relax(dt_vd / N, 3)
+        out.append([g.field(w) for w in (ox.FIELD_ALPHA, ox.FIELD_P, ox.FIELD_U, ox.FIELD_U + 2)])
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
+def test_energy_exit_test_matches_oracle():
+    """The energy exit test (relative change per sub-step of sigma A + kinetic
+    energy of u_cr, the Section 6 variant): the GPU FP64 path and the oracle
+    give the same test values and stop at the same k_f (a tolerance the first
+    sub-step passes, and one no sub-step passes), and the fields agree to
+    1e-10."""
+    for tol, k_expect in ((1e-4, 1), (5e-5, 40)):
+        c = inputs.random_small_case(13, 31, 17, sigma=0.002)
+        c.params.update(conv_mode=inputs.CONV_AREA, conv_tol=tol)
+        dt_cfl, dt_b, dt_vd, N = oracle.timesteps(c.params, 0.02)
+        g = ox.Oscar(c.params, c.solid, c.alpha0)
+        o = oracle.OracleState(c.params, c.solid, c.alpha0)
+        g.drag_step(dt_vd)
+        o.drag_step(dt_vd)
+        _, kg, tg = g.relax(dt_vd / 40, 40)
+        _, ko, hist = o.relax(dt_vd / 40, 40)
+        assert kg == ko == k_expect
+        assert tg == pytest.approx(hist[-1], rel=1e-6)
+        compare(g, o, 2, 1e-10)

@@ -608,3 +608,72 @@ def test_smoothing_is_area_weighted_on_anisotropic_cells():
     als, _, _ = oracle.stage_interface(p, s, a)
     expect = x ** 2 + hx ** 2 * hy / (2 * (hy + hx))
     np.testing.assert_allclose(als[2:-2, 1:-1], np.tile(expect[1:-1], (ny - 4, 1)), rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Section 6: interface area (energy-based relaxation exit test)
+# ---------------------------------------------------------------------------
+def test_interface_area_of_a_sharp_flat_interface_is_the_channel_height():
+    """A sharp planar interface across a 2D channel: the two cells beside the
+    step each have |grad alpha| = 0.5/h (face values 1, 0.5 and 0.5, 0), so the
+    area is exactly the height; in 3D the cross-section."""
+    for dim, shape in ((2, (10, 16)), (3, (6, 5, 16))):
+        p = inputs.default_params(dim=dim, nx=16, ny=shape[-2], nz=shape[0] if dim == 3 else 1,
+                                  hx=2e-6, hy=2e-6, hz=2e-6)
+        a = np.zeros(shape)
+        a[..., :7] = 1.0
+        A = oracle.stage_interface_area(p, np.zeros(shape, np.uint8), a)
+        expect = shape[-2] * 2e-6 * (shape[0] * 2e-6 if dim == 3 else 1.0)
+        assert A == pytest.approx(expect, rel=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_interface_area_of_a_smooth_disc_and_sphere(dim):
+    """A smooth (tanh) disc or sphere of radius R: the area tends to the
+    perimeter 2 pi R (2D) or the surface 4 pi R^2 (3D)."""
+    n, R = (64, 16.0) if dim == 2 else (40, 10.0)
+    d = inputs.static_drop(n=n, R_cells=R, dim=dim, profile="tanh", width_cells=1.5)
+    A = oracle.stage_interface_area(d.params, d.solid, d.alpha0)
+    h = d.params["hx"]
+    expect = 2 * math.pi * R * h if dim == 2 else 4 * math.pi * (R * h) ** 2
+    assert A == pytest.approx(expect, rel=0.03)
+
+
+def test_relax_energy_closed_forms():
+    """Energy of the Section 6 test: sigma times the area of a sharp planar
+    interface (the channel height) at rest; a uniform velocity u0 in one fluid
+    (alpha = 0, no interface) gives rho2 u0^2 / 2 times the fluid volume;
+    solid cells do not count."""
+    p = inputs.default_params(dim=2, nx=16, ny=10, hx=2e-6, hy=2e-6, sigma=0.03, rho1=700.0, rho2=1000.0)
+    solid = np.zeros((10, 16), np.uint8)
+    a = np.zeros((10, 16))
+    a[:, :7] = 1.0
+    zero = [np.zeros((10, 16))] * 2
+    assert oracle.stage_relax_energy(p, solid, a, zero) == pytest.approx(0.03 * 10 * 2e-6, rel=1e-12)
+    solid[0, :] = 1
+    u = [np.full((10, 16), 0.2), np.full((10, 16), -0.1)]
+    e = oracle.stage_relax_energy(p, solid, np.zeros((10, 16)), u)
+    assert e == pytest.approx(0.5 * 1000.0 * 0.05 * (9 * 16) * 4e-12, rel=1e-12)
+
+
+def test_energy_exit_test_stops_a_field_at_rest():
+    """With the energy test (Section 6 reading) a field at rest whose interface
+    does not move (no surface tension, no flow) exits after the first
+    sub-step."""
+    c = inputs.static_drop(n=16, R_cells=4.0, theta_deg=90.0, sigma=0.0)
+    p = dict(c.params, conv_mode=2, conv_tol=1e-9, U_inlet=1e-3)
+    st = oracle.OracleState(p, c.solid, c.alpha0)
+    rc, kf, hist = st.relax(1e-8, 20)
+    assert kf == 1 and hist[0] < 1e-12
+
+
+def test_energy_exit_test_runs_on_while_a_drop_relaxes():
+    """A square drop with surface tension, released from rest: the capillary
+    flow it starts changes the energy, so the test does not pass at once."""
+    c = inputs.static_drop(n=24, R_cells=6.0, theta_deg=90.0, sigma=0.03)
+    a = np.zeros_like(c.alpha0)
+    a[6:18, 6:18] = 1.0
+    p = dict(c.params, conv_mode=2, conv_tol=5e-6, U_inlet=1e-3)
+    st = oracle.OracleState(p, c.solid, a)
+    rc, kf, hist = st.relax(1e-8, 5)
+    assert kf == 5 and min(hist) > 5e-6
