@@ -103,6 +103,7 @@ typedef struct {
     size_t device_bytes;      /* device memory held by the handle */
     long long kernel_launches; /* CUDA kernels launched by this handle since creation */
     int mg_first_cta_level;   /* first multigrid level held in one CTA's shared memory */
+    int mg_cta_global_level;  /* level worked by that CTA with coefficients in global memory, -1 when none */
 } oscar_stats_t;
 
 typedef struct oscar_instance *oscar_handle;

@@ -599,6 +599,7 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out) {
     out->device_bytes = I.arena_bytes;
     out->kernel_launches = I.nexec;
     out->mg_first_cta_level = I.lc0;
+    out->mg_cta_global_level = I.lg;
     return 0;
 }
 

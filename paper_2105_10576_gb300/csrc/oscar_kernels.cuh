@@ -1692,7 +1692,9 @@ __global__ void k_mg_diag(GridD g, const uint8_t *__restrict__ fluid, MG3<M> cc,
 // level); the residual for the restriction is formed cell-parallel first.
 constexpr int kCtaThreads = 1024;
 constexpr int kExactCells = 128;   // coarsest CTA level solved exactly when at most this size
-constexpr int kGlCells = 16384;    // largest level the CTA works with global coefficients
+constexpr int kGlCells = 2048;     // largest level the CTA works with global coefficients (larger ones
+                                   // ran slower there than as per-level launches: 4 or more cells per
+                                   // thread and seven L2 loads per cell and sweep)
 template <typename M> struct CLevel {
     GridD g;
     const M *c[3];          // global face coefficients

@@ -53,7 +53,7 @@ class oscar_stats_t(C.Structure):
         ("cg_iters_total", C.c_longlong), ("cg_iters_last", C.c_int), ("mg_levels", C.c_int),
         ("phase_volume", C.c_double), ("n_fluid", C.c_longlong), ("cell_updates", C.c_longlong),
         ("device_bytes", C.c_size_t), ("kernel_launches", C.c_longlong),
-        ("mg_first_cta_level", C.c_int),
+        ("mg_first_cta_level", C.c_int), ("mg_cta_global_level", C.c_int),
     ]
 
 

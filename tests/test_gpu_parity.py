@@ -505,6 +505,7 @@ def test_schedule_changes_speed_not_the_solution():
                                                 coarse_refresh=1, block_x=32)):
         g = ox.Oscar(p, c.solid, c.alpha0)
         g.set_schedule(sched)
+        sched = dict(autotune.DEFAULT, **sched)
         assert g.schedule() == sched
         g.drag_step(dt_vd)
         g.relax(dt_vd / N, 3)
@@ -526,7 +527,8 @@ def test_coarse_cta_with_global_level_is_the_same_vcycle():
     b in shared memory, coefficients from global memory) performs the same
     operations as the per-level kernels: the fields after a drag step and
     relaxation sub-steps are bitwise equal with and without it (mixed path,
-    3D grid whose 2880-cell level qualifies)."""
+    3D grid; with the CTA holding the levels of at most 256 cells, the
+    360-cell level above them qualifies)."""
     c = inputs.random_small_case(12, 48, 24, nz=20, dim=3)
     c.params.update(conv_mode=inputs.CONV_PRES_RESID, conv_tol=0.0)
     p = dict(c.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
@@ -534,7 +536,9 @@ def test_coarse_cta_with_global_level_is_the_same_vcycle():
     out = []
     for flag in (1, 0):
         g = ox.Oscar(p, c.solid, c.alpha0)
-        g.set_schedule(dict(cta_global=flag))
+        g.set_schedule(dict(cta_global=flag, cta_cells=256))
+        st = g.stats()
+        assert (st["mg_cta_global_level"] == st["mg_first_cta_level"] - 1) if flag else st["mg_cta_global_level"] == -1
         g.drag_step(dt_vd)
         g.relax(dt_vd / N, 3)
         out.append([g.field(w) for w in (ox.FIELD_ALPHA, ox.FIELD_P, ox.FIELD_U, ox.FIELD_U + 2)])
