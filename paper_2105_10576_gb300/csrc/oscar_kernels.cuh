@@ -942,17 +942,19 @@ __global__ void k_phistar_rhs(GridD g, const uint32_t *__restrict__ info, C3<T> 
 }
 
 // corrected flux of the face of direction A at face coordinates (i,j,k):
-// phi = phi* - c_f (q_H - q_L), the pressure difference taken in FP64 (q = 0
-// beyond the outlet face), unchanged on walls and at the inlet
+// phi = phi* - c_f (q_H - q_L), the pressure difference taken in FP64 and
+// rounded to T (q = 0 beyond the outlet face), unchanged on walls and at the
+// inlet. dq: the rounded difference of this face when it is interior (the
+// caller forms it once for the flux and the velocity correction).
 template <int A, typename T>
 __device__ __forceinline__ T corrected_face(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
                                             const T *__restrict__ phisA, const T *__restrict__ cfA,
-                                            const double *__restrict__ q) {
+                                            const double *__restrict__ q, T dq) {
     int L, H;
     const int t = decode_face<A>(g, info, i, j, k, L, H);
     const int f = flo(g, A, i, j, k);
     const T ps = phisA[f];
-    if (t == FT_INTERIOR) return ps - cfA[f] * (T)(q[H] - q[L]);
+    if (t == FT_INTERIOR) return ps - cfA[f] * dq;
     if (t == FT_OUTLET) return ps - cfA[f] * (T)(0.0 - q[L]);
     return ps;
 }
@@ -960,31 +962,44 @@ __device__ __forceinline__ T corrected_face(const GridD &g, const uint32_t *__re
 template <int A, typename T>
 __device__ __forceinline__ void correct_pair(const GridD &g, const uint32_t *__restrict__ info, int i, int j, int k,
                                              const T *__restrict__ phisA, const T *__restrict__ cfA,
-                                             const double *__restrict__ q, T *__restrict__ phiA) {
-    phiA[flo(g, A, i, j, k)] = corrected_face<A, T>(g, info, i, j, k, phisA, cfA, q);
+                                             const double *__restrict__ q, T dlo, T *__restrict__ phiA) {
+    phiA[flo(g, A, i, j, k)] = corrected_face<A, T>(g, info, i, j, k, phisA, cfA, q, dlo);
     const int qq = A == 0 ? i : (A == 1 ? j : k), n = A == 0 ? g.nx : (A == 1 ? g.ny : g.nz);
-    if (qq == n - 1)
-        phiA[fhi(g, A, i, j, k)] = corrected_face<A, T>(g, info, i + (A == 0), j + (A == 1), k + (A == 2), phisA, cfA, q);
+    if (qq == n - 1)   // the domain's last face of the line is never interior
+        phiA[fhi(g, A, i, j, k)] =
+            corrected_face<A, T>(g, info, i + (A == 0), j + (A == 1), k + (A == 2), phisA, cfA, q, T(0));
 }
 
 // flux correction of every face and velocity correction v = HbyA + (1/A)
-// reconstruct(face accelerations) (Section 2.2) in one cell kernel
+// reconstruct(face accelerations) (Section 2.2) in one cell kernel. Each
+// interior face's pressure difference (T)(q_H - q_L) is formed once per cell
+// that uses it: the low faces' by the cell, the high face in x taken from the
+// next lane (the next cell of the row: a warp never spans two rows, block x
+// extents being multiples of 32), the other high faces formed again. FP64
+// instructions are scarce on this GPU, and this halves them.
 template <int DIM, typename T>
 __global__ void k_correct(GridD g, const uint32_t *__restrict__ info, C3<T> phis, C3<T> cf, const double *__restrict__ q,
                           P3<T> phi, C3<T> hbya, const T *__restrict__ rA, C3<T> fst, P3<T> v) {
     griddep_wait();
     CELL_IJK(g);
+    const uint32_t inf = inside ? info[c] : 0u;
+    const bool fluid = (inf & INFO_FLUID) != 0;
+    const double qc = fluid ? q[c] : 0.0;
+    T dlo[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+        if (fluid && ftype(inf, a, 0) == FT_INTERIOR) dlo[a] = (T)(qc - q[c - noff(g, a)]);
+    const T dnext = __shfl_down_sync(0xffffffffu, dlo[0], 1);
     if (!inside) return;
-    correct_pair<0, T>(g, info, i, j, k, phis.a[0], cf.a[0], q, phi.a[0]);
-    correct_pair<1, T>(g, info, i, j, k, phis.a[1], cf.a[1], q, phi.a[1]);
-    if constexpr (DIM == 3) correct_pair<2, T>(g, info, i, j, k, phis.a[2], cf.a[2], q, phi.a[2]);
-    const uint32_t inf = info[c];
-    if (!(inf & INFO_FLUID)) {
+    correct_pair<0, T>(g, info, i, j, k, phis.a[0], cf.a[0], q, dlo[0], phi.a[0]);
+    correct_pair<1, T>(g, info, i, j, k, phis.a[1], cf.a[1], q, dlo[1], phi.a[1]);
+    if constexpr (DIM == 3) correct_pair<2, T>(g, info, i, j, k, phis.a[2], cf.a[2], q, dlo[2], phi.a[2]);
+    if (!fluid) {
 #pragma unroll
         for (int a = 0; a < DIM; ++a) v.a[a][c] = T(0);
         return;
     }
-    const double qc = q[c];
+    const bool next_in_warp = (threadIdx.x & 31) != 31;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
         const int off = noff(g, a);
@@ -994,10 +1009,12 @@ __global__ void k_correct(GridD g, const uint32_t *__restrict__ info, C3<T> phis
         for (int s = 0; s < 2; ++s) {
             const int t = ftype(inf, a, s);
             if (t == FT_INTERIOR) {
-                const int nb = s ? c + off : c - off;
                 const int f = s ? fhi(g, a, i, j, k) : flo(g, a, i, j, k);
-                const double qL = s ? qc : q[nb], qH = s ? q[nb] : qc;
-                gs += fst.a[a][f] - (T)(qH - qL) / ha;
+                T dq;
+                if (s == 0) dq = dlo[a];
+                else if (a == 0 && next_in_warp) dq = dnext;
+                else dq = (T)(q[c + off] - qc);
+                gs += fst.a[a][f] - dq / ha;
             } else if (t == FT_OUTLET) {
                 gs += -(T)(0.0 - qc) / (T(0.5) * ha);
             }
