@@ -810,9 +810,10 @@ __global__ void k_vel_grad(GridD g, const uint32_t *__restrict__ info, C3<T> v, 
 
 // HbyA = H/A: old-time term, neighbour part of the viscous Laplacian, inflow
 // (implicit upwind) neighbours, explicit linear-upwind correction and the
-// transpose viscous term.
+// transpose viscous term. A latency-bound gather: the register cap (6 blocks
+// of 256 threads per SM instead of 4) keeps more loads in flight.
 template <int DIM, typename T>
-__global__ void k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, C3<T> phic,
+__global__ void __launch_bounds__(256, 6) k_momentum_H(GridD g, const uint32_t *__restrict__ info, C3<T> v, C3<T> vold, C3<T> phic,
                              const T *__restrict__ alpha, const T *__restrict__ rA, Fluid<T> fl, T vin0, T dt,
                              C3<T> G0, C3<T> G1, C3<T> G2, P3<T> hbya) {
     griddep_wait();
