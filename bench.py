@@ -109,6 +109,8 @@ def kernel_bytes(name: str, c, e: int):
         return n * (e + 8 + 8 + 8 + 2 * e + 4) + F * e
     if base == "k_cg_init":          # q, b, r64 in/out, FP64 face coefficients
         return n * (8 + 8 + 8 + 2 * e + 4) + 8 * F
+    if base == "k_correct":          # phi*, c_f, f_st in and phi out per face; q (FP64), info, HbyA, 1/A in, v out
+        return 4 * F * e + n * (8 + 4 + 3 * e + e + 3 * e)
     return None
 
 
@@ -140,7 +142,8 @@ def recorded_traffic(kernel: str):
     files = {"k_mg_rbgs": "k_mg_rbgs_constriction_3d.md", "k_cg_pz_apply": "k_cg_pz_apply_constriction_3d.md",
              "k_cg_update": "k_cg_update_constriction_3d.md",
              "k_mg_resid_restrict": "k_mg_resid_restrict_constriction_3d.md",
-             "k_momentum_H": "k_momentum_H_constriction_3d.md"}
+             "k_momentum_H": "k_momentum_H_constriction_3d.md", "k_cg_init": "k_cg_init_constriction_3d.md",
+             "k_cg_refine": "k_cg_refine_constriction_3d.md", "k_correct": "k_correct_constriction_3d.md"}
     base = kernel.split("<")[0]
     if base not in files:
         return None
