@@ -1597,45 +1597,68 @@ __global__ void k_mg_rbgs_dot(GridD g, MG3<M> cc, const M *__restrict__ idiag, M
 
 // coarse b = sum over children of the fine residual b - M x. With first set,
 // the coarse x receives the first colour-0 half sweep from x = 0
-// (x = b / diagonal on colour 0, 0 on colour 1), else x = 0. The coarsening
-// ratios are template parameters so the children unroll and their loads
-// overlap.
+// (x = b / diagonal on colour 0, 0 on colour 1), else x = 0. One thread per
+// fine cell: a block covers a tile of whole coarse cells (even extents,
+// kRRTile), puts the residuals of its fine cells in shared memory, and one
+// thread per coarse cell of the tile sums the children in the order x fastest.
+// On the small middle levels this spreads a launch over 8x the threads of a
+// thread-per-coarse-cell kernel, whose chain of child loads set its latency.
+template <int DIM> struct RRTile {
+    static constexpr int X = 32, Y = DIM == 3 ? 4 : 8, Z = DIM == 3 ? 2 : 1;
+};
 template <int DIM, typename M, int RX, int RY, int RZ>
-__global__ void k_mg_resid_restrict(GridD gf, GridD gc, const uint8_t *__restrict__ fluid, MG3<M> cc,
-                                    const M *__restrict__ diag, const M *__restrict__ x, const M *__restrict__ b,
-                                    M *__restrict__ bc, M *__restrict__ xc, const M *__restrict__ idc, int first) {
-    CELL_IJK(gc);
-    constexpr int NCH = RX * RY * RZ;
-    M w[NCH][2 * DIM], dg[NCH];
-    uint8_t fl[NCH];
+__global__ void __launch_bounds__(256) k_mg_resid_restrict(GridD gf, GridD gc, const uint8_t *__restrict__ fluid,
+                                                           MG3<M> cc, const M *__restrict__ diag,
+                                                           const M *__restrict__ x, const M *__restrict__ b,
+                                                           M *__restrict__ bc, M *__restrict__ xc,
+                                                           const M *__restrict__ idc, int first) {
+    constexpr int TX = RRTile<DIM>::X, TY = RRTile<DIM>::Y, TZ = RRTile<DIM>::Z;
+    constexpr int CX = TX / RX, CY = TY / RY, CZ = TZ / RZ, NC = CX * CY * CZ;
+    __shared__ M res[TX * TY * TZ];
+    const int t = threadIdx.x + TX * (threadIdx.y + TY * threadIdx.z);
+    const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y, k = blockIdx.z * TZ + threadIdx.z;
+    const bool in = i < gf.nx && j < gf.ny && k < gf.nz;
+    const int cell = i + gf.nx * (j + gf.ny * k);
+    M w[2 * DIM], dg = M(0);
+    uint8_t fl = 0;
+    if (in) {
+        fl = fluid[cell];
+        dg = diag[cell];
+        mg_row_coeffs<DIM, M>(gf, cc, i, j, k, w);
+    }
+    int ic = 0, jc = 0, kc = 0;
+    bool cin = false;
     M idq = M(0);
-    if (inside) {
-#pragma unroll
-        for (int q = 0; q < NCH; ++q) {
-            const int ii = i * RX + q % RX, jj = j * RY + (q / RX) % RY, kk = k * RZ + q / (RX * RY);
-            fl[q] = 0;
-            if (ii < gf.nx && jj < gf.ny && kk < gf.nz) {
-                const int cell = ii + gf.nx * (jj + gf.ny * kk);
-                fl[q] = fluid[cell];
-                dg[q] = diag[cell];
-                mg_row_coeffs<DIM, M>(gf, cc, ii, jj, kk, w[q]);
-            }
-        }
-        if (first) idq = idc[c];
+    if (t < NC) {
+        ic = blockIdx.x * CX + t % CX;
+        jc = blockIdx.y * CY + (t / CX) % CY;
+        kc = blockIdx.z * CZ + t / (CX * CY);
+        cin = ic < gc.nx && jc < gc.ny && kc < gc.nz;
+        if (cin && first) idq = idc[ic + gc.nx * (jc + gc.ny * kc)];
     }
     griddep_wait();
-    if (!inside) return;
+    M rv = M(0);
+    if (in) {
+        rv = b[cell] - (dg * x[cell] - mg_row_off<DIM, M>(gf, w, x, cell, i, j, k));
+        rv = fl ? rv : M(0);
+    }
+    res[t] = rv;
+    __syncthreads();
+    if (!cin) return;
     M acc = M(0);
 #pragma unroll
-    for (int q = 0; q < NCH; ++q) {
-        const int ii = i * RX + q % RX, jj = j * RY + (q / RX) % RY, kk = k * RZ + q / (RX * RY);
-        if (ii >= gf.nx || jj >= gf.ny || kk >= gf.nz) continue;
-        const int cell = ii + gf.nx * (jj + gf.ny * kk);
-        const M rv = b[cell] - (dg[q] * x[cell] - mg_row_off<DIM, M>(gf, w[q], x, cell, ii, jj, kk));
-        acc += fl[q] ? rv : M(0);
-    }
-    bc[c] = acc;
-    xc[c] = (first && ((i + j + k) & 1) == 0) ? acc * idq : M(0);
+    for (int qz = 0; qz < RZ; ++qz)
+#pragma unroll
+        for (int qy = 0; qy < RY; ++qy)
+#pragma unroll
+            for (int qx = 0; qx < RX; ++qx) {
+                const int ii = ic * RX + qx, jj = jc * RY + qy, kk = kc * RZ + qz;
+                if (ii >= gf.nx || jj >= gf.ny || kk >= gf.nz) continue;
+                acc += res[(ii - (int)blockIdx.x * TX) + TX * ((jj - (int)blockIdx.y * TY) + TY * (kk - (int)blockIdx.z * TZ))];
+            }
+    const int cq = ic + gc.nx * (jc + gc.ny * kc);
+    bc[cq] = acc;
+    xc[cq] = (first && ((ic + jc + kc) & 1) == 0) ? acc * idq : M(0);
 }
 
 static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, int rz, const uint8_t *__restrict__ ff,

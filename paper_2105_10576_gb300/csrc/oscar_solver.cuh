@@ -361,9 +361,10 @@ template <typename T> struct Impl {
 
     template <int DIM, int RX, int RY, int RZ>
     static void rr_launch(Instance &I, const Level &L, const Level &C, const M *x, const M *b, M *bc, M *xc, int first) {
-        L3 LC = launch3(C.g);
-        launchk(k_mg_resid_restrict<DIM, M, RX, RY, RZ>, LC.grid, LC.block, 0, I.stream, to_dev(L.g), to_dev(C.g),
-                L.fluid, mg3(L), (const M *)L.diag, x, b, bc, xc, (const M *)C.idiag, first);
+        using TT = RRTile<DIM>;
+        const dim3 grid((L.g.nx + TT::X - 1) / TT::X, (L.g.ny + TT::Y - 1) / TT::Y, (L.g.nz + TT::Z - 1) / TT::Z);
+        launchk(k_mg_resid_restrict<DIM, M, RX, RY, RZ>, grid, dim3(TT::X, TT::Y, TT::Z), 0, I.stream, to_dev(L.g),
+                to_dev(C.g), L.fluid, mg3(L), (const M *)L.diag, x, b, bc, xc, (const M *)C.idiag, first);
         ++I.nlaunch;
     }
     // fused residual + restriction (+ the coarse level's first colour-0 half
