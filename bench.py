@@ -182,6 +182,51 @@ def kernel_table(entries, c, e):
     return rows, tot
 
 
+def in_graph_sweep_time(ox, c, sched, dt_vd, dt_cr, nsub, stream, steps=3, rounds=2):
+    """In-graph duration of the finest-level red-black half sweep, by
+    difference: two identical instances run the same OSCAR steps from their
+    CUDA graphs, the second with every plain finest-level half sweep issued
+    twice (oscar_profile_repeat; the repeat rewrites the values just written,
+    so both instances stay bitwise equal and take the same PCG iterations).
+    The extra time over the extra launches, both timed with CUDA events on the
+    bench stream around whole steps, is one sweep's duration in the step, with
+    its operands where the step leaves them (in L2 on this workload)."""
+    import torch
+    sims = [ox.Oscar(c.params, c.solid, c.alpha0, stream=stream.cuda_stream) for _ in range(2)]
+    try:
+        for q, s_ in enumerate(sims):
+            if sched is not None:
+                s_.set_schedule(sched)
+            s_.profile_repeat(q == 1)
+            s_.drag_step(dt_vd)          # untimed: builds the graphs
+            s_.relax(dt_cr, nsub)
+        torch.cuda.synchronize()
+        ms, launches, iters = [0.0, 0.0], [0, 0], [0, 0]
+        for _ in range(rounds):
+            for q, s_ in enumerate(sims):
+                st0 = s_.stats()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    s_.drag_step(dt_vd)
+                    s_.relax(dt_cr, nsub)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                st1 = s_.stats()
+                ms[q] += e0.elapsed_time(e1)
+                launches[q] += st1["kernel_launches"] - st0["kernel_launches"]
+                iters[q] += st1["cg_iters_total"] - st0["cg_iters_total"]
+        extra = launches[1] - launches[0]
+        if iters[0] != iters[1] or extra <= 0:
+            return None
+        return {"avg_launch_us": 1e3 * (ms[1] - ms[0]) / extra, "extra_launches": extra,
+                "step_ms": ms[0] / (rounds * steps), "pcg_iterations": iters[0]}
+    finally:
+        for s_ in sims:
+            s_.close()
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -829,6 +874,21 @@ def main():
                                   "with the largest total; algorithmic bytes per launch / average launch time",
                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
                         else "fallback"}
+
+        # the same kernel's in-graph duration, by difference (see in_graph_sweep_time)
+        if roofline is not None and args.workload == "constriction_3d":
+            ig = in_graph_sweep_time(ox, c, sched, dt_vd, dt_cr, min(nsub, 8), stream)
+            if ig is not None:
+                fine = f"k_mg_rbgs<{c.params['dim']}, {'double' if es == 8 else 'float'}, false>"
+                ab = kernel_bytes(fine, c, es)
+                ig.update({"kernel": fine + " (finest level)", "algorithmic_bytes_per_launch": ab,
+                           "achieved": ab / (ig["avg_launch_us"] * 1e-6) / 1e9,
+                           "method": "two identical instances stepped from their CUDA graphs, the second with every "
+                                     "plain finest-level half sweep issued twice (idempotent, fields bitwise equal, "
+                                     "same PCG iterations); extra time / extra launches, CUDA events on the bench "
+                                     "stream; operands L2-resident in the step, so this is an L2-assisted rate"})
+                ig["frac"] = ig["achieved"] / peak
+                roofline["in_graph"] = ig
 
     sim_sched = sim.schedule()
 

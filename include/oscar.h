@@ -252,6 +252,19 @@ int oscar_profile(oscar_handle h, int enable);
 int oscar_profile_read(oscar_handle h, int index, int *count_out, char *name_out, size_t name_cap,
                        unsigned *grid_out, double *total_ms, long long *launches);
 
+/* In-graph kernel timing by difference (measurement support, not part of the
+ * method). enable = 1 makes the following step calls issue every finest-level
+ * red-black half sweep that is not fused with a dot product twice in a row:
+ * a half sweep reads only the other colour, so the repeat writes the values
+ * just written and the fields stay bitwise those of a normal step. The steps
+ * run from their (rebuilt) CUDA graphs as usual; the time they add over the
+ * same steps of an identical instance, divided by the launches they add
+ * (oscar_stats kernel_launches), is the in-graph duration of one such sweep
+ * with its operands where the step leaves them. enable = 0 restores normal
+ * steps. Waits for the stream. OSCAR_E_INVALID_ARG while an asynchronous step
+ * is pending. */
+int oscar_profile_repeat(oscar_handle h, int enable);
+
 /* Phase volume sum over fluid cells of alpha * cell_volume, computed without
  * allocating any device memory. The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc, such as code running while

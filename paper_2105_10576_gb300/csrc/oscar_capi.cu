@@ -347,6 +347,7 @@ int oscar_create(const oscar_params *p, const uint8_t *solid, const double *alph
     I.cta_cells = 1024;
     I.block_x = 0;
     I.cta_global = 1;
+    I.repeat_fine = 0;
     I.lg = -1;
     long long nf = 0;
     for (int c = 0; c < I.g.ncell; ++c) nf += solid[c] == 0;
@@ -606,6 +607,21 @@ int oscar_stats(oscar_handle h, oscar_stats_t *out) {
 }  // extern "C"
 
 extern "C" {
+
+int oscar_profile_repeat(oscar_handle h, int enable) {
+    if (!h) return OSCAR_E_INVALID_ARG;
+    Instance &I = h->I;
+    if (I.pending >= 0) return OSCAR_E_INVALID_ARG;   // a launched step awaits oscar_wait
+    int rc = sync_bounded(I.stream, kSyncTimeoutSec);
+    if (rc) return rc;
+    const int v = enable ? 1 : 0;
+    if (v != I.repeat_fine) {   // the launch sequence changes: graphs are captured again
+        I.repeat_fine = v;
+        if (I.prec == OSCAR_FP64) Solver<double>::release_graphs(I);
+        else Solver<float>::release_graphs(I);
+    }
+    return 0;
+}
 
 int oscar_profile(oscar_handle h, int enable) {
     if (!h) return OSCAR_E_INVALID_ARG;

@@ -146,6 +146,7 @@ struct Instance {
     long long cell_updates;
     int mg_nu, mg_nu_c, mg_coarse_sweeps;   // sweeps on the finest level, on coarser levels, on the coarsest
     int mg_nu_cta;         // sweeps on the levels held by the coarse CTA
+    int repeat_fine;       // measurement: finest-level plain half sweeps issued twice (oscar_profile_repeat)
     int coarse_refresh;    // the coarsest level's inverse is formed every this many PISO set-ups
     int cta_cells;         // levels of at most this many cells go to the coarse CTA
     int block_x;           // cap on the x extent of cell-kernel blocks (0: none)

@@ -345,8 +345,9 @@ template <typename T> struct Impl {
             launchk(k_mg_rbgs_dot<DIM, M>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b, colour,
                     I.partials, I.ticket, I.scal), ++I.nlaunch;
         else
-            launchk(k_mg_rbgs<DIM, M, false>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x, b,
-                    colour, g, 0, 0, 0, (const M *)nullptr), ++I.nlaunch;
+            for (int rep = 0; rep < (l == 0 && I.repeat_fine ? 2 : 1); ++rep)   // a repeat is idempotent
+                launchk(k_mg_rbgs<DIM, M, false>, LL.grid, LL.block, 0, I.stream, g, mg3(L), (const M *)L.idiag, x,
+                        b, colour, g, 0, 0, 0, (const M *)nullptr), ++I.nlaunch;
     }
     // the first post-smoothing half sweep (colour 1) of level l with the
     // prolongation from level l + 1 (x of level l + 1 in xc) folded in

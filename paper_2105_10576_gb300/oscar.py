@@ -61,8 +61,8 @@ EXPORTS = ["oscar_timesteps", "oscar_create", "oscar_drag_step", "oscar_relax", 
            "oscar_drag_step_async", "oscar_relax_async", "oscar_standard_step_async", "oscar_wait",
            "oscar_footprint", "oscar_query",
            "oscar_fields", "oscar_fields_device", "oscar_set_field", "oscar_stats", "oscar_destroy",
-           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_get_schedule", "oscar_set_schedule",
-           "oscar_phase_volume_noalloc"]
+           "oscar_strerror", "oscar_profile", "oscar_profile_read", "oscar_profile_repeat", "oscar_get_schedule",
+           "oscar_set_schedule", "oscar_phase_volume_noalloc"]
 
 _lib = None
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
     lib.oscar_strerror.argtypes = [C.c_int]
     lib.oscar_strerror.restype = C.c_char_p
     lib.oscar_profile.argtypes = [H, C.c_int]
+    lib.oscar_profile_repeat.argtypes = [H, C.c_int]
     lib.oscar_profile_read.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.c_char_p, C.c_size_t,
                                        C.POINTER(C.c_uint), dp, C.POINTER(C.c_longlong)]
     lib.oscar_phase_volume_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_longlong, C.c_double, C.c_void_p,
@@ -244,6 +245,11 @@ class Oscar:
         """Start (clearing the last recording) or stop in-step kernel timing:
         while on, steps run eagerly with CUDA events around every launch."""
         _check(self.lib.oscar_profile(self.h, 1 if enable else 0), "oscar_profile")
+
+    def profile_repeat(self, enable: bool):
+        """Issue every plain finest-level half sweep twice (idempotent) in the
+        following graph steps, for in-graph timing by difference."""
+        _check(self.lib.oscar_profile_repeat(self.h, 1 if enable else 0), "oscar_profile_repeat")
 
     def profile_read(self) -> list:
         """[(kernel name, grid blocks, total ms, launches)] of the recording."""

@@ -547,6 +547,28 @@ def test_coarse_cta_with_global_level_is_the_same_vcycle():
         assert np.array_equal(x, y)
 
 
+def test_profile_repeat_keeps_the_fields():
+    """The in-graph timing mode (every plain finest-level half sweep issued
+    twice) leaves the fields bitwise equal to normal steps, with the same PCG
+    iterations and more kernel launches (mixed path, 3D)."""
+    c = inputs.random_small_case(17, 40, 20, nz=16, dim=3)
+    p = dict(c.params, precision=inputs.PREC_MIXED, cg_rtol=1e-8)
+    dt_cfl, dt_b, dt_vd, N = ox.oscar_timesteps(p, 0.02)
+    out, st = [], []
+    for rep in (False, True):
+        g = ox.Oscar(p, c.solid, c.alpha0)
+        g.profile_repeat(rep)
+        g.drag_step(dt_vd)
+        g.relax(dt_vd / N, 3)
+        out.append([g.field(w) for w in (ox.FIELD_ALPHA, ox.FIELD_P, ox.FIELD_U)])
+        st.append(g.stats())
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+    assert st[0]["cg_iters_total"] == st[1]["cg_iters_total"]
+    assert st[1]["kernel_launches"] > st[0]["kernel_launches"]
+
+
 def test_energy_exit_test_matches_oracle():
     """The energy exit test (relative change per sub-step of sigma A + kinetic
     energy of u_cr, the Section 6 variant): the GPU FP64 path and the oracle
