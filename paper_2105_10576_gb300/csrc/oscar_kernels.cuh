@@ -1676,16 +1676,15 @@ static __global__ void k_mg_fluid_coarsen(GridD gf, GridD gc, int rx, int ry, in
     fc[c] = any;
 }
 
-// coarse face coefficient of direction A: sum of the fine faces covering it,
-// halved across a coarsened direction
+// coarse face coefficient of direction A at face coordinates (i,j,k) of the
+// coarse grid: sum of the fine faces covering it, halved across a coarsened
+// direction
 template <int A, typename M>
-__global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, const M *__restrict__ cfine,
-                                  M *__restrict__ ccoarse) {
-    griddep_wait();
-    FACE_IJK(gc, A);
-    int rr[3] = {rx, ry, rz};
-    int nfn[3] = {gf.nx, gf.ny, gf.nz};
-    int base[3] = {i, j, k};
+__device__ __forceinline__ M coarse_face(const GridD &gf, int i, int j, int k, int rx, int ry, int rz,
+                                         const M *__restrict__ cfine) {
+    const int rr[3] = {rx, ry, rz};
+    const int nfn[3] = {gf.nx, gf.ny, gf.nz};
+    const int base[3] = {i, j, k};
     int lo[3], cnt[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
@@ -1701,7 +1700,38 @@ __global__ void k_mg_coarse_coeff(GridD gf, GridD gc, int rx, int ry, int rz, co
     for (int oz = 0; oz < cnt[2]; ++oz)
         for (int oy = 0; oy < cnt[1]; ++oy)
             for (int ox = 0; ox < cnt[0]; ++ox) acc += cfine[flo(gf, A, lo[0] + ox, lo[1] + oy, lo[2] + oz)];
-    ccoarse[f] = rr[A] == 2 ? M(0.5) * acc : acc;
+    return rr[A] == 2 ? M(0.5) * acc : acc;
+}
+
+// A coarse level's operator in one cell kernel: the face coefficients from
+// the finer level's (coarse_face; each face stored by the cell it is the low
+// face of, or by the last cell of its line) and the diagonal with its
+// reciprocal, as k_mg_diag forms them from the stored faces. The high faces
+// a cell needs for its diagonal are formed again with the same arithmetic,
+// so the values are those of a face pass followed by a diagonal pass.
+template <int A, typename M>
+__device__ __forceinline__ M coarse_face_pair(const GridD &gf, const GridD &gc, int i, int j, int k, int rx, int ry,
+                                              int rz, const M *__restrict__ cfine, M *__restrict__ ccoarse) {
+    const M lo = coarse_face<A, M>(gf, i, j, k, rx, ry, rz, cfine);
+    const M hi = coarse_face<A, M>(gf, i + (A == 0), j + (A == 1), k + (A == 2), rx, ry, rz, cfine);
+    ccoarse[flo(gc, A, i, j, k)] = lo;
+    const int q = A == 0 ? i : (A == 1 ? j : k), n = A == 0 ? gc.nx : (A == 1 ? gc.ny : gc.nz);
+    if (q == n - 1) ccoarse[fhi(gc, A, i, j, k)] = hi;
+    return lo + hi;
+}
+template <int DIM, typename M>
+__global__ void k_mg_level_operator(GridD gf, GridD gc, int rx, int ry, int rz, MG3<M> cfine, P3<M> ccoarse,
+                                    const uint8_t *__restrict__ fluid, M *__restrict__ diag, M *__restrict__ idiag) {
+    griddep_wait();
+    CELL_IJK(gc);
+    if (!inside) return;
+    M acc = M(0);
+    acc += coarse_face_pair<0, M>(gf, gc, i, j, k, rx, ry, rz, cfine.a[0], ccoarse.a[0]);
+    acc += coarse_face_pair<1, M>(gf, gc, i, j, k, rx, ry, rz, cfine.a[1], ccoarse.a[1]);
+    if constexpr (DIM == 3) acc += coarse_face_pair<2, M>(gf, gc, i, j, k, rx, ry, rz, cfine.a[2], ccoarse.a[2]);
+    if (!fluid[c]) { diag[c] = M(0); idiag[c] = M(0); return; }
+    diag[c] = acc;
+    idiag[c] = acc > M(0) ? M(1) / acc : M(0);
 }
 
 // diagonal (sum of the face coefficients) and its reciprocal (0 on solid cells

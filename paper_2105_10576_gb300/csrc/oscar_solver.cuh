@@ -228,25 +228,17 @@ template <typename T> struct Impl {
         for (int l = 0; l < I.nlev; ++l) {
             Level &L = I.lev[l];
             GridD g = to_dev(L.g);
-            if (l > 0) {
-                Level &F = I.lev[l - 1];
-                GridD gf = to_dev(F.g);
-                for (int a = 0; a < DIM; ++a) {
-                    L3 FL = launch3_faces(L.g, a);
-                    if (a == 0)
-                        launchk(k_mg_coarse_coeff<0, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
-                                                                                  (const M *)F.c[0], (M *)L.c[0]), ++I.nlaunch;
-                    else if (a == 1)
-                        launchk(k_mg_coarse_coeff<1, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
-                                                                                  (const M *)F.c[1], (M *)L.c[1]), ++I.nlaunch;
-                    else
-                        launchk(k_mg_coarse_coeff<2, M>, FL.grid, FL.block, 0, I.stream, gf, g, F.r[0], F.r[1], F.r[2],
-                                                                                  (const M *)F.c[2], (M *)L.c[2]), ++I.nlaunch;
-                }
-            }
             L3 LL = launch3(L.g);
-            launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag,
-                    (M *)L.idiag), ++I.nlaunch;
+            if (l == 0) {
+                launchk(k_mg_diag<DIM, M>, LL.grid, LL.block, 0, I.stream, g, L.fluid, mg3(L), (M *)L.diag,
+                        (M *)L.idiag), ++I.nlaunch;
+            } else {
+                Level &F = I.lev[l - 1];
+                P3<M> cc;
+                for (int a = 0; a < 3; ++a) cc.a[a] = (M *)L.c[a];
+                launchk(k_mg_level_operator<DIM, M>, LL.grid, LL.block, 0, I.stream, to_dev(F.g), g, F.r[0], F.r[1],
+                        F.r[2], mg3(F), cc, (const uint8_t *)L.fluid, (M *)L.diag, (M *)L.idiag), ++I.nlaunch;
+            }
         }
         {   // the coarse CTA's shared-memory image for this set of coefficients
             CLevels<M> P;
