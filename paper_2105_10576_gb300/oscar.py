@@ -227,11 +227,16 @@ class Oscar:
             sh = self.shape
         return int(np.prod(sh)), sh
 
-    def field(self, which: int) -> np.ndarray:
+    def field(self, which: int, out: np.ndarray = None) -> np.ndarray:
+        """The field as float64 in host memory; `out` (optional, contiguous
+        float64 of the field's size, e.g. a view of pinned memory) receives it."""
         n, sh = self._len_shape(which)
-        out = np.zeros(sh)
+        if out is None:
+            out = np.zeros(sh)
+        elif out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or out.size != n:
+            raise ValueError("out must be a contiguous float64 array of the field's size")
         _check(self.lib.oscar_fields(self.h, which, out.ctypes.data_as(C.POINTER(C.c_double)), n), "oscar_fields")
-        return out
+        return out.reshape(sh)
 
     def field_device(self, which: int, dev_ptr: int, n: int):
         _check(self.lib.oscar_fields_device(self.h, which, C.c_void_p(dev_ptr), n), "oscar_fields_device")
