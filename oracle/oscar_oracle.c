@@ -649,7 +649,7 @@ int or_poisson_banded(const or_grid *g, double *const cf[3], const double *b, do
 }
 
 /* Normalised L1 residual of M q = b: sum|b - Mq| / (sum|Mq - M qbar| + sum|b - M qbar| + 1e-20),
- * qbar the mean of q over fluid cells (Section 3.2, "normalized norm"). */
+ * qbar the mean of q over fluid cells (the normalised residual norm of Section 3.2). */
 double or_normalised_residual(const or_grid *g, double *const cf[3], const double *b, const double *q) {
     int nc = g->ncell;
     double *Mq = calloc(nc, sizeof(double));
