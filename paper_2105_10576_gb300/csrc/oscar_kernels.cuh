@@ -395,6 +395,7 @@ __device__ __forceinline__ void set_cond(int *ctl, cudaGraphConditionalHandle h,
 // later check of the defect-correction loop (mixed path)
 constexpr int kMaxOuter = 40;          // defect-correction trips (mixed path)
 constexpr double kInnerRtol = 1e-4;    // FP32 inner solve: residual reduction per trip
+constexpr double kTripMargin = 0.5;    // ... or down to this fraction of the outer target
 __device__ __forceinline__ void residual_control(double *scal, int *ctl, double rtol, int mode,
                                                  cudaGraphConditionalHandle h) {
     double bn = sqrt(scal[S_BB]), rn = sqrt(scal[S_RR]);
@@ -417,7 +418,12 @@ __device__ __forceinline__ void residual_control(double *scal, int *ctl, double 
     }
     bool more = !bad && rn > scal[S_TARGET];
     if (more && ctl[C_OUT] >= kMaxOuter) { ctl[C_NOTCONV] = 1; more = false; }
-    scal[S_ITARGET] = kInnerRtol * rn;
+    // the FP32 trip stops at kInnerRtol times its starting residual, or as
+    // soon as half the outer target is reached (solving below what the FP64
+    // test asks for is wasted; the factor 2 covers the drift of the FP32
+    // recursive residual from the true one, and a trip that still ends above
+    // the target is followed by another)
+    scal[S_ITARGET] = fmax(kInnerRtol * rn, kTripMargin * scal[S_TARGET]);
     set_cond(ctl, h, more);
 }
 
